@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Hermite-leapfrog benchmark on GB300.
+
+Workload (one bench "step"): 2D acoustics on the periodic unit square, 512 x 512
+nodes per grid, m = 3 (16 scaled derivatives per node and field component), FP64,
+seeded Gaussian pressure pulse of width 0.05, 200 leapfrog steps at C_CFL = 0.9.
+Metric: DOF-updates/s = (dim+1) (m+1)^dim N^dim * leapfrog steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hl|reference]
+
+--impl hl (default): the CUDA library through its C ABI.  `value` is device time
+(CUDA events on the library's stream) with the state resident in HBM, L2 flushed
+between timed steps; `e2e` is the same work timed on the host through
+hl_set_initial / hl_step / hl_get_fields with pinned host buffers.
+--impl reference: the CPU oracle (plain C, FP64, OpenMP over nodes) on the host
+cores, each step a bounded sample (one leapfrog step of the same 512^2 problem).
+Under torchrun every rank solves its own independently seeded problem (no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Hermite-leapfrog DOF-updates/s vs FP64 plain at equal L2 error; % roofline"
+UNIT = "DOF-updates/s"
+DIM, M, N, LF_STEPS = 2, 3, 512, 200
+L2_FLUSH_BYTES = 256 << 20
+
+# FP64 peak of one GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per SM
+# per clock x 2 flop x 2.070 GHz maximum SM clock.
+N_SM = 152
+FP64_FMA_PER_SM_CLK = 2
+SM_MAX_GHZ = 2.070
+FP64_PEAK_FLOPS = N_SM * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9
+
+# DRAM traffic of the dominant kernel per launch from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
+# source is unchanged (keyed by the hash of the kernel header).
+TRAFFIC_SOURCE_HASH = None
+TRAFFIC_BYTES = {"p_half": None, "u_half": None}
+
+WORKLOAD = ("2D acoustics p_t+div u=0, u_t+grad p=0, periodic unit square, 512x512 nodes per grid, "
+            "m=3 (16 scaled derivatives per node per field), FP64, seeded Gaussian pressure pulse "
+            "(width 0.05, random centre), 200 leapfrog steps per bench step at C_CFL=0.9")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["hl", "reference"], default="hl")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dofs():
+    return (DIM + 1) * (M + 1) ** DIM * N ** DIM
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("hl_fp64.cuh", "hl_fp64_dispatch.cuh"):
+        with open(os.path.join(ROOT, "paper_1808_10481_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis and vis.split(",")[0].isdigit():
+                cmd += ["-i", vis.split(",")[0]]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_sample(target_s: float = 15.0):
+    """The oracle as it stands on the host cores: leapfrog steps of the same problem."""
+    import oracle
+    from paper_1808_10481_gb300 import inputs as I
+    ncell = [N] * DIM
+    dt = I.cfl_dt(ncell)
+    st = I.gaussian_pulse(DIM, M, ncell, dt, seed=1)
+    t0 = time.perf_counter()
+    p, u = oracle.run(DIM, M, ncell, dt, st.p, st.u, 1)
+    t1 = time.perf_counter() - t0
+    extra = max(0, int(target_s / max(t1, 1e-9)) - 1)
+    t0 = time.perf_counter()
+    if extra:
+        oracle.run(DIM, M, ncell, dt, p, u, extra)
+    t2 = time.perf_counter() - t0
+    steps = 1 + extra
+    secs = t1 + t2
+    return {"value": dofs() * steps / secs, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{steps} leapfrog step(s) of the 512^2 m=3 problem in {secs:.1f} s "
+                      f"(plain C oracle, OpenMP over nodes)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1808_10481_gb300 import inputs as I
+    ncell = [N] * DIM
+    dt = I.cfl_dt(ncell)
+    st = I.gaussian_pulse(DIM, M, ncell, dt, seed=1)
+    p, u = st.p, st.u
+    for _ in range(args.warmup):
+        p, u = oracle.run(DIM, M, ncell, dt, p, u, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p, u = oracle.run(DIM, M, ncell, dt, p, u, 1)
+    secs = time.perf_counter() - t0
+    value = dofs() * args.steps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "each step = 1 leapfrog step of the 512^2 problem",
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"{args.steps} timed leapfrog steps of the 512^2 m=3 problem"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import build as libbuild
+    from paper_1808_10481_gb300 import hl
+    from paper_1808_10481_gb300 import inputs as I
+
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    hl.load()
+
+    ncell = [N] * DIM
+    dt = I.cfl_dt(ncell)
+    st = I.gaussian_pulse(DIM, M, ncell, dt, seed=1 + rank)
+    stream = torch.cuda.current_stream()
+    h = hl.hl_create(DIM, M, ncell, dt)
+    hl.hl_set_stream(h, stream)
+    hl.hl_set_initial(h, st.p, st.u)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        hl.hl_step(h, LF_STEPS)
+        flush.fill_(1)
+    hl.hl_sync(h)
+    hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
+    hl.hl_kernel_times(h)  # reset
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler()
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        hl.hl_step(h, LF_STEPS)
+        ends[k].record(stream)
+        flush.fill_(k & 0xFF)          # untimed: evicts the state from L2 between steps
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock = clocks.stop()
+    status = hl.hl_sync(h)
+    if status != hl.HL_OK:
+        raise SystemExit(f"solver reported status {status}")
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ktimes, kcount = hl.hl_kernel_times(h)
+    hl.hl_set_option(h, hl.HL_OPT_TIMING, 0)
+
+    t_max_ms = dev_ms
+    if dist:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max_ms = float(t.item())
+    value = world * dofs() * LF_STEPS * args.steps / (t_max_ms / 1e3)
+
+    # roofline of the dominant kernel (FP64 pipe): algorithmic flops per launch / mean launch time
+    fma, add = hl.hl_op_counts(DIM, M)
+    nnode = N ** DIM
+    nz = fma / 2.0
+    bfly = DIM * (1 << DIM) * (M + 1) ** DIM
+    flops = {"p_half": nnode * (2 * nz + DIM * bfly), "u_half": nnode * (2 * nz + bfly)}
+    dom = max(("p_half", "u_half"), key=lambda k: ktimes[k])
+    mean_s = ktimes[dom] / kcount[dom] / 1e3
+    achieved = flops[dom] / mean_s
+    traffic = TRAFFIC_BYTES.get(dom) if TRAFFIC_SOURCE_HASH == kernel_hash() else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic, "kernel": dom,
+                "kernel_mean_us": mean_s * 1e6,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.070 GHz (unit counts and max clock)",
+                "kernel_share": ktimes[dom] / max(dev_ms, 1e-9)}
+
+    # end to end through the C ABI with pinned host buffers
+    nq = (M + 1) ** DIM
+    hp = torch.empty((nnode, nq), dtype=torch.float64, pin_memory=True)
+    hu = torch.empty((DIM, nnode, nq), dtype=torch.float64, pin_memory=True)
+    hp.copy_(torch.from_numpy(st.p))
+    hu.copy_(torch.from_numpy(st.u))
+    op = torch.empty_like(hp).pin_memory()
+    ou = torch.empty_like(hu).pin_memory()
+    e2e_n = max(1, min(args.steps, 5))
+    hl.hl_set_initial(h, hp, hu)
+    hl.hl_step(h, LF_STEPS)
+    hl.hl_get_fields(h, op, ou)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_n):
+        hl.hl_set_initial(h, hp, hu)
+        hl.hl_step(h, LF_STEPS)
+        hl.hl_get_fields(h, op, ou)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * dofs() * LF_STEPS * e2e_n / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": hp.numel() * 8 + hu.numel() * 8,
+           "d2h_bytes_per_step": op.numel() * 8 + ou.numel() * 8}
+    hl.hl_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": DIM, "m": M, "n_cells": ncell,
+                       "leapfrog_steps_per_step": LF_STEPS, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}: one independently seeded problem per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+            "gpu_launches": int(kcount["p_half"] + kcount["u_half"] + kcount["small"]),
+            "kernel_ms": ktimes,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * hl.h -- C ABI of the GB300 Hermite-leapfrog solver (libhl.so).
+ *
+ * Method: Vargas, Hagstrom, Chan, Warburton, "Leapfrog time-stepping for
+ * Hermite methods", arXiv 1808.10481.
+ *
+ * The solver advances the first-order acoustics system
+ *     p_t + div u = 0,   u_t + grad p = 0            (unit wave speed)
+ * on the periodic unit box [0,1)^dim.  This is the paper's system
+ * p_t = c div v, v_t = c grad p (Section 2, eq. waveModel; Section 3.1.2,
+ * eq. wavend) with c = 1 and v = -u, and the sign form of its experiments
+ * (Section 4, Section 5, Section 6).
+ *
+ * Grids and data (Section 2, eqs. pGrid and dGrid; Section 5):
+ *   - each axis k has n_k nodes per grid and spacing h_k = 1/n_k;
+ *   - primal node j sits at j*h_k and carries p; dual node j sits at
+ *     (j + 1/2)*h_k and carries all dim velocity components;
+ *   - every node carries the scaled derivatives
+ *         f~_a = prod_k h_k^{a_k} / a_k! * d^a f,   0 <= a_k <= m,
+ *     i.e. nq = (m+1)^dim values per node per field component;
+ *   - p is held at t = n*dt and u at t = (n + 1/2)*dt (Section 2: the
+ *     staggered start, p at t0 and v at t0 + dt/2).
+ *
+ * One step (Section 2, eqs. update1, LFloop, final1; Section 3.1.2, eqs. pdup
+ * and vdup; Section 5, eq. lf1update2D): for every primal node, build the
+ * tensor-product Hermite-Birkhoff interpolant of degree 2m+1 per axis of u
+ * on the cell whose 2^dim vertices are the surrounding dual nodes (Section 2,
+ * eq. interp), evaluate its exact Cauchy-Kowalevsky evolution at the node over
+ * +-dt/2 and update p (the p-half); then do the same for every dual node with
+ * the interpolant of the new p and update u (the u-half).
+ *
+ * HOST LAYOUT (hl_set_initial, hl_get_fields):
+ *   p[node][q], u[comp][node][q], row-major double, with
+ *   node = ix + n_0*(iy + n_1*iz) and q = a_0 + (m+1)*(a_1 + (m+1)*a_2).
+ * DEVICE LAYOUT (hl_bind_device, hl_set_initial_device, hl_get_fields_device
+ * use the host layout; hl_bind_device uses this one):
+ *   p[q][node], u[comp][q][node] ("slot-major"), double.
+ *
+ * Errors: every int-returning call returns HL_OK (0) or a negative code.
+ * hl_last_error() gives a human-readable message for the last failure on a
+ * handle.  After HL_ECUDA or HL_ETIMEOUT a handle is poisoned: later calls
+ * return HL_ESTATE until hl_destroy.  A handle must not be used from two
+ * host threads at once; distinct handles are independent.
+ *
+ * Streams: all device work of a handle is issued on its stream (the legacy
+ * default stream unless hl_set_stream was called).  hl_step is stream-ordered
+ * and does not synchronise; hl_get_fields and hl_sync do.
+ *
+ * Ownership: the library never frees memory it did not allocate.  Device
+ * buffers bound with hl_bind_device stay owned by the caller and must outlive
+ * the handle (or the next hl_bind_device call).
+ */
+#ifndef HL_H
+#define HL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hl_solver hl_solver;
+
+enum {
+    HL_OK = 0,
+    HL_EINVAL = -1,      /* invalid argument                                   */
+    HL_ENOMEM = -2,      /* device or host allocation failed                   */
+    HL_ECUDA = -3,       /* a CUDA call failed (handle poisoned)               */
+    HL_ETIMEOUT = -4,    /* a bounded device wait expired (handle poisoned)    */
+    HL_ENONFINITE = -5,  /* a NaN or Inf appeared in the updated node data     */
+    HL_ESTATE = -6       /* call not valid in the handle's state               */
+};
+
+/* Arithmetic modes for hl_set_precision. */
+enum {
+    HL_FP64 = 0          /* every operation in IEEE binary64                   */
+};
+
+/*
+ * hl_create -- allocate a solver for the periodic unit box.
+ *   dim     : 1, 2 or 3 (Section 2 for dim = 1; Section 5 for the tensor grids).
+ *   m       : Hermite order, 0 <= m <= 6 (the paper runs up to m = 6 in
+ *             Section 5.3); dim = 3 allows m <= 3.
+ *   n_cells : dim entries, nodes per axis per grid, each >= 2.
+ *   dt      : time step, 0 < dt < min_k h_k.  The update is the exact
+ *             evolution of the interpolant only while c*dt/dx < 1 (Section 3,
+ *             the remark before eq. ph1evolve); C_CFL = dt/min h_k = 0.9 is
+ *             the paper's usual choice (Section 4, Tables 1-5).
+ *   out     : receives the handle (set to NULL on failure).
+ * Returns HL_EINVAL on bad arguments (before any CUDA call), HL_ENOMEM or
+ * HL_ECUDA if device set-up fails.  The state is zero after creation.
+ */
+int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out);
+
+/*
+ * hl_set_initial -- copy host initial data (host layout) to the device.
+ *   p : prod(n_cells)*nq doubles, p at t = 0.
+ *   u : dim*prod(n_cells)*nq doubles, u at t = dt/2.
+ * Resets the step counter to 0.  Synchronous with respect to the host
+ * buffers (they may be reused on return).  Pinned host memory is fastest.
+ */
+int hl_set_initial(hl_solver *h, const double *p, const double *u);
+
+/*
+ * hl_set_initial_device / hl_get_fields_device -- as hl_set_initial /
+ * hl_get_fields but with DEVICE pointers in the host layout; stream-ordered,
+ * no host synchronisation.
+ */
+int hl_set_initial_device(hl_solver *h, const double *p_dev, const double *u_dev);
+int hl_get_fields_device(hl_solver *h, double *p_dev, double *u_dev);
+
+/*
+ * hl_step -- advance n_steps >= 0 full steps (p-half then u-half each;
+ * Section 6 counts one such p-and-v pass as an iteration).  Stream-ordered;
+ * returns after enqueueing.  A NaN/Inf produced by the update is reported by
+ * the next hl_sync / hl_get_fields as HL_ENONFINITE.
+ */
+int hl_step(hl_solver *h, int64_t n_steps);
+
+/*
+ * hl_get_fields -- copy the state to host buffers (host layout) and
+ * synchronise.  Any pointer may be NULL to skip that output.
+ *   t_p receives n*dt (time of p), t_u receives (n + 1/2)*dt (time of u).
+ * Returns HL_ENONFINITE if any update since the last check produced a
+ * non-finite value (the data are still copied).
+ */
+int hl_get_fields(hl_solver *h, double *p, double *u, double *t_p, double *t_u);
+
+/*
+ * hl_sync -- wait for the handle's stream and report the device status
+ * (HL_OK, HL_ENONFINITE, or HL_ECUDA).  Clears the non-finite flag.
+ */
+int hl_sync(hl_solver *h);
+
+/* hl_destroy -- release everything the library allocated for h (NULL is a no-op). */
+void hl_destroy(hl_solver *h);
+
+/* hl_last_error -- message for the last failure on h (never NULL; "" if none). */
+const char *hl_last_error(const hl_solver *h);
+
+/*
+ * hl_set_stream -- issue the handle's device work on cuda_stream (a
+ * cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream); NULL selects
+ * the legacy default stream.  Synchronises the previous stream first.
+ */
+int hl_set_stream(hl_solver *h, void *cuda_stream);
+
+/*
+ * hl_bind_device -- make the solver operate in place on caller-owned device
+ * buffers in the DEVICE layout (slot-major): p_dev[q][node] (nq*nnode
+ * doubles) and u_dev[comp][q][node] (dim*nq*nnode doubles), each 16-byte
+ * aligned.  The current contents of the bound buffers become the state
+ * (no copy); the step counter is kept.  Passing NULL for both returns to
+ * library-owned buffers (state zeroed).
+ */
+int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev);
+
+/*
+ * hl_set_precision -- select the arithmetic mode (HL_FP64 only for now).
+ */
+int hl_set_precision(hl_solver *h, int mode);
+
+/* Options for hl_set_option. */
+enum {
+    HL_OPT_KERNEL_PATH = 1,  /* 0 = automatic; 1 = one persistent CTA with the
+                                whole state in shared memory (tiny grids only);
+                                2 = one grid launch per half-step             */
+    HL_OPT_TIMING = 2        /* 1 = bracket every kernel launch with CUDA events
+                                on the handle's stream (read by hl_kernel_times);
+                                0 = off (default)                             */
+};
+
+/*
+ * hl_set_option -- set an execution option (see the HL_OPT_* values).
+ * Returns HL_EINVAL for an unknown option or value.  Options change how the
+ * work is scheduled, never what is computed.
+ */
+int hl_set_option(hl_solver *h, int option, int64_t value);
+
+/*
+ * hl_kernel_times -- durations of the kernel launches recorded while
+ * HL_OPT_TIMING was on, since the previous call (which resets them).
+ * Synchronises the handle's stream.
+ *   ms[3]       : total milliseconds of p-half launches, u-half launches and
+ *                 single-CTA whole-run launches (any pointer may be NULL);
+ *   launches[3] : the matching launch counts.
+ */
+int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches);
+
+/*
+ * hl_op_counts -- floating-point work of the FP64 kernels per node and full
+ * step for (dim, m): multiply-adds (one multiply-add = 2 flops) and plain
+ * additions of the vertex butterflies.  Used for roofline accounting.
+ */
+int hl_op_counts(int dim, int m, double *fma_per_node_step, double *add_per_node_step);
+
+/*
+ * hl_info -- sizes of a handle: nnode (nodes per grid), nq ((m+1)^dim) and
+ * the number of completed steps.  Any pointer may be NULL.
+ */
+int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HL_H */

@@ -57,6 +57,9 @@ def _load():
     lib.oracle_half_step.restype = None
     lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, dp, dp, ctypes.c_int64]
     lib.oracle_run.restype = None
+    lib.oracle_half_step_nodes.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, ctypes.c_int, dp, dp,
+                                            i64p, ctypes.c_int64, dp]
+    lib.oracle_half_step_nodes.restype = None
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_threads.restype = ctypes.c_int
     _lib = lib
@@ -112,6 +115,26 @@ def half_step(d: int, m: int, ncell, dt: float, mode: int, src: np.ndarray, dst:
                          _dptr(_h_array(m)), mode, _dptr(src), _dptr(dst))
 
 
+def half_step_nodes(d: int, m: int, ncell, dt: float, mode: int, src: np.ndarray, dst: np.ndarray,
+                    nodes) -> np.ndarray:
+    """The half-step at the listed target nodes only; returns (ncomp_dst, len(nodes), nq).
+
+    src/dst are full fields in host layout (dst is not modified)."""
+    lib = _load()
+    nq = (m + 1) ** d
+    ncd = 1 if mode == 0 else d
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    dst = np.ascontiguousarray(dst, dtype=np.float64)
+    out = np.empty((ncd, nodes.size, nq), dtype=np.float64)
+    nc = np.array(list(ncell) + [1] * (3 - len(ncell)), dtype=np.int64)
+    lam = lambdas(ncell, dt)
+    lib.oracle_half_step_nodes(d, m, nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(lam),
+                               _dptr(_h_array(m)), mode, _dptr(src), _dptr(dst),
+                               nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nodes.size, _dptr(out))
+    return out
+
+
 def run(d: int, m: int, ncell, dt: float, p: np.ndarray, u: np.ndarray, n_steps: int):
     """n_steps leapfrog steps; returns new (p, u) arrays (inputs untouched).
 
@@ -129,6 +152,6 @@ def run(d: int, m: int, ncell, dt: float, p: np.ndarray, u: np.ndarray, n_steps:
 
 
 __all__ = [
-    "build", "node_update", "half_step", "run", "lambdas", "set_threads", "threads",
+    "build", "node_update", "half_step", "half_step_nodes", "run", "lambdas", "set_threads", "threads",
     "hermite_inverse", "hermite_inverse_exact", "interp_system",
 ]

@@ -228,6 +228,54 @@ void oracle_half_step(int d, int m, const int64_t *ncell, const double *lam, con
     }
 }
 
+/* The half-step of oracle_half_step evaluated only at the listed target nodes:
+ * out[(c*n_sample + k)*nq + q] = dst[c][nodes[k]][q] + increment, with the
+ * same gather and node update.  dst is read only.  Used to check a large run
+ * at sampled nodes from its own state one half-step earlier. */
+void oracle_half_step_nodes(int d, int m, const int64_t *ncell, const double *lam, const double *H,
+                            int mode, const double *src, const double *dst, const int64_t *nodes,
+                            int64_t n_sample, double *out)
+{
+    const int n = m + 1;
+    const int64_t nq = ipow(n, d);
+    const int64_t nv = (int64_t)1 << d;
+    int64_t N[ORC_MAXD] = {1, 1, 1};
+    int64_t nnode = 1;
+    for (int k = 0; k < d; ++k) { N[k] = ncell[k]; nnode *= N[k]; }
+    const int ncs = mode == 0 ? d : 1;
+    const int ncd = mode == 0 ? 1 : d;
+    const int lo_off = mode == 0 ? -1 : 0;
+
+#pragma omp parallel for schedule(static)
+    for (int64_t smp = 0; smp < n_sample; ++smp) {
+        const int64_t node = nodes[smp];
+        int64_t j[ORC_MAXD] = {0, 0, 0};
+        int64_t t = node;
+        for (int k = 0; k < d; ++k) { j[k] = t % N[k]; t /= N[k]; }
+        double *vtx = (double *)malloc(sizeof(double) * (size_t)(ncs * nv * nq));
+        double *inc = (double *)malloc(sizeof(double) * (size_t)(ncd * nq));
+        for (int64_t v = 0; v < nv; ++v) {
+            int64_t vn = 0, stride = 1;
+            for (int k = 0; k < d; ++k) {
+                int64_t jk = j[k] + lo_off + ((v >> k) & 1);
+                jk = ((jk % N[k]) + N[k]) % N[k];
+                vn += jk * stride;
+                stride *= N[k];
+            }
+            for (int c = 0; c < ncs; ++c)
+                for (int64_t q = 0; q < nq; ++q)
+                    vtx[((int64_t)c * nv + v) * nq + q] = src[((int64_t)c * nnode + vn) * nq + q];
+        }
+        oracle_node_update(d, m, lam, H, mode, vtx, inc);
+        for (int c = 0; c < ncd; ++c)
+            for (int64_t q = 0; q < nq; ++q)
+                out[((int64_t)c * n_sample + smp) * nq + q] =
+                    dst[((int64_t)c * nnode + node) * nq + q] + inc[(int64_t)c * nq + q];
+        free(vtx);
+        free(inc);
+    }
+}
+
 /* n_steps full steps: p-half then u-half (p at t -> t+dt, u at t+dt/2 -> t+3dt/2). */
 void oracle_run(int d, int m, const int64_t *ncell, const double *lam, const double *H,
                 double *p, double *u, int64_t n_steps)

@@ -1,0 +1,350 @@
+// FP64 Hermite-leapfrog half-step kernels for sm_103a.
+//
+// One thread owns one target node.  For the p-half the partner field is u
+// (dim components) on the dual grid; for the u-half it is p on the primal
+// grid (Section 2, eqs. final1/LFloop; Section 3.1.2, eqs. pdup/vdup).
+//
+// The fused per-node operator.  Composing the per-axis Hermite-Birkhoff
+// inverse H (Section 2, eq. interp; the tensor product of Section 5) with the
+// Cauchy-Kowalevsky series gives, for direction i, a linear map from the
+// 2^dim vertex blocks to the (m+1)^dim outputs.  Reflecting the cell about its
+// centre along axis k swaps the two vertices on that axis and flips the sign
+// of odd derivatives; the series term is odd along axis i and even along the
+// other axes.  Hence the block of vertex v equals the block of the all-lower
+// vertex times prod_{k: v_k = 1} sigma_k with sigma_k = (-1)^(s_k + l_k + [k==i]).
+// So the kernel first forms the 2^dim sums/differences of the vertex values
+// (a Walsh-Hadamard butterfly over the vertices) and then contracts each
+// output slot s with a single (m+1)^dim operator M0_i, picking for every
+// (s, l) the butterfly entry whose per-axis sum/difference choice matches the
+// parity above.  This needs (m+1)^(2 dim) instead of 2^dim (m+1)^(2 dim)
+// multiply-adds per direction.
+//
+// Structural zeros of M0_i: if l_k = 0 on some axis k with t = s_k + [k==i]
+// even and t >= 2, every coefficient index a_k >= t on that axis is even and
+// >= 2, and constant end data feed no even coefficient of degree >= 2, so the
+// entry vanishes.  The host verifies the rule on the computed operator; the
+// kernels skip those entries at compile time.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hl {
+
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+
+template <int D, int M>
+struct Shape {
+    static constexpr int n = M + 1;                 // slots per axis
+    static constexpr int NQ = ipow_c(n, D);         // slots per node
+    static constexpr int NV = 1 << D;               // cell vertices
+    static constexpr int NCOEF = D * NQ * NQ;       // dense (i, l, s) table
+    // the table travels in the kernel parameter bank when it fits
+    static constexpr bool kParam = NCOEF * 8 <= 28 * 1024;
+    // the u-half keeps all dim output blocks live only when they fit in registers
+    static constexpr bool kUFused = D * NQ <= 96;
+};
+
+__host__ __device__ constexpr bool coef_nonzero(int D, int n, int i, int s, int l)
+{
+    for (int k = 0; k < D; ++k) {
+        const int sk = s % n, lk = l % n;
+        s /= n;
+        l /= n;
+        const int t = sk + (k == i ? 1 : 0);
+        if (lk == 0 && (t % 2) == 0 && t >= 2) return false;
+    }
+    return true;
+}
+
+// butterfly entry for (i, s, l): bit k set = difference (lower - upper) on axis k
+__host__ __device__ constexpr int bfly_pattern(int D, int n, int i, int s, int l)
+{
+    int pat = 0;
+    for (int k = 0; k < D; ++k) {
+        const int sk = s % n, lk = l % n;
+        s /= n;
+        l /= n;
+        if ((sk + lk + (k == i ? 1 : 0)) & 1) pat |= 1 << k;
+    }
+    return pat;
+}
+
+__host__ __device__ constexpr int coef_index(int NQ, int i, int l, int s) { return (i * NQ + l) * NQ + s; }
+
+// Coefficient table holder: by value in the parameter bank, or a global pointer.
+template <int D, int M, bool P = Shape<D, M>::kParam>
+struct CoefArg;
+template <int D, int M>
+struct CoefArg<D, M, true> {
+    double v[Shape<D, M>::NCOEF];
+    __device__ __forceinline__ double get(int idx) const { return v[idx]; }
+};
+template <int D, int M>
+struct CoefArg<D, M, false> {
+    const double *__restrict__ v;
+    __device__ __forceinline__ double get(int idx) const { return __ldg(v + idx); }
+};
+
+struct GridDesc {
+    int n[3];        // nodes per axis (1 for unused axes)
+    int64_t nnode;   // n0*n1*n2
+};
+
+// In-place Walsh-Hadamard butterfly over the 2^D vertex values:
+// afterwards x[pat] = sum_v prod_{k: v_k=1} (bit k of pat ? -1 : +1) x_v.
+template <int D>
+__device__ __forceinline__ void butterfly(double *x)
+{
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+        for (int v = 0; v < (1 << D); ++v) {
+            if (!(v & (1 << k))) {
+                const double a = x[v], b = x[v | (1 << k)];
+                x[v] = a + b;
+                x[v | (1 << k)] = a - b;
+            }
+        }
+    }
+}
+
+// Node index of the 2^D cell vertices on the partner grid.  lo = -1 for the
+// p-half (dual nodes j-1, j), 0 for the u-half (primal nodes j, j+1).
+template <int D>
+__device__ __forceinline__ void vertex_nodes(const GridDesc &g, int64_t node, int lo, int *vtx)
+{
+    int j[3] = {0, 0, 0};
+    int64_t t = node;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        j[k] = (int)(t % g.n[k]);
+        t /= g.n[k];
+    }
+    int lower[3], upper[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        int a = j[k] + lo, b = j[k] + lo + 1;
+        if (a < 0) a += g.n[k];
+        if (b >= g.n[k]) b -= g.n[k];
+        lower[k] = a;
+        upper[k] = b;
+    }
+#pragma unroll
+    for (int v = 0; v < (1 << D); ++v) {
+        int idx = 0, stride = 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            idx += ((v >> k) & 1 ? upper[k] : lower[k]) * stride;
+            stride *= g.n[k];
+        }
+        vtx[v] = idx;
+    }
+}
+
+__device__ __forceinline__ void report_nonfinite(bool bad, unsigned *status)
+{
+    const unsigned mask = __activemask();
+    const unsigned votes = __ballot_sync(mask, bad);
+    if (votes && (threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) atomicOr(status, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// p-half at one primal node: P[s] += sum_i sum_l coef(i,l,s) * bfly_i,l[pattern]
+// (the host stores the coefficients already negated: p_new = p_old - series).
+// Loads go through `ld(comp, slot, vertex_node)`.
+template <int D, int M, class C, class Ld>
+__device__ __forceinline__ void p_node(const C &coef, const Ld &ld, const int *vtx, double *out)
+{
+    using S = Shape<D, M>;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int l = 0; l < S::NQ; ++l) {
+            double x[S::NV];
+#pragma unroll
+            for (int v = 0; v < S::NV; ++v) x[v] = ld(i, l, vtx[v]);
+            butterfly<D>(x);
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) {
+                if (coef_nonzero(D, S::n, i, s, l))
+                    out[s] = fma(coef.get(coef_index(S::NQ, i, l, s)), x[bfly_pattern(D, S::n, i, s, l)], out[s]);
+            }
+        }
+    }
+}
+
+// u-half at one dual node, directions I0..I0+NI-1: out[(i-I0)*NQ + s].
+template <int D, int M, int I0, int NI, class C, class Ld>
+__device__ __forceinline__ void u_node(const C &coef, const Ld &ld, const int *vtx, double *out)
+{
+    using S = Shape<D, M>;
+#pragma unroll
+    for (int l = 0; l < S::NQ; ++l) {
+        double x[S::NV];
+#pragma unroll
+        for (int v = 0; v < S::NV; ++v) x[v] = ld(0, l, vtx[v]);
+        butterfly<D>(x);
+#pragma unroll
+        for (int ii = 0; ii < NI; ++ii) {
+            const int i = I0 + ii;
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) {
+                if (coef_nonzero(D, S::n, i, s, l))
+                    out[ii * S::NQ + s] =
+                        fma(coef.get(coef_index(S::NQ, i, l, s)), x[bfly_pattern(D, S::n, i, s, l)], out[ii * S::NQ + s]);
+            }
+        }
+    }
+}
+
+struct GlobalLd {
+    const double *__restrict__ base;
+    int64_t slot_stride;   // nnode
+    int nq;
+    __device__ __forceinline__ double operator()(int comp, int slot, int node) const
+    {
+        return __ldg(base + (int64_t)(comp * nq + slot) * slot_stride + node);
+    }
+};
+
+struct SharedLd {
+    const double *base;
+    int slot_stride;
+    int nq;
+    __device__ __forceinline__ double operator()(int comp, int slot, int node) const
+    {
+        return base[(comp * nq + slot) * slot_stride + node];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Grid kernels: one launch per half-step.
+template <int D, int M, class C>
+__global__ void __launch_bounds__(128) k_p_half(const double *__restrict__ U, double *__restrict__ P, GridDesc g,
+                                                C coef, unsigned *status)
+{
+    using S = Shape<D, M>;
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= g.nnode) return;
+    int vtx[S::NV];
+    vertex_nodes<D>(g, node, -1, vtx);
+    double out[S::NQ];
+#pragma unroll
+    for (int s = 0; s < S::NQ; ++s) out[s] = P[(int64_t)s * g.nnode + node];
+    GlobalLd ld{U, g.nnode, S::NQ};
+    p_node<D, M>(coef, ld, vtx, out);
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < S::NQ; ++s) {
+        P[(int64_t)s * g.nnode + node] = out[s];
+        bad |= !isfinite(out[s]);
+    }
+    report_nonfinite(bad, status);
+}
+
+template <int D, int M, int I0, int NI, class C>
+__global__ void __launch_bounds__(128) k_u_half(const double *__restrict__ P, double *__restrict__ U, GridDesc g,
+                                                C coef, unsigned *status)
+{
+    using S = Shape<D, M>;
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= g.nnode) return;
+    int vtx[S::NV];
+    vertex_nodes<D>(g, node, 0, vtx);
+    double out[NI * S::NQ];
+#pragma unroll
+    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+        for (int s = 0; s < S::NQ; ++s) out[ii * S::NQ + s] = U[(int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node];
+    GlobalLd ld{P, g.nnode, S::NQ};
+    u_node<D, M, I0, NI>(coef, ld, vtx, out);
+    bool bad = false;
+#pragma unroll
+    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+        for (int s = 0; s < S::NQ; ++s) {
+            U[(int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node] = out[ii * S::NQ + s];
+            bad |= !isfinite(out[ii * S::NQ + s]);
+        }
+    report_nonfinite(bad, status);
+}
+
+// u-half of the small kernel one direction at a time (when dim blocks do not fit in registers)
+template <int D, int M, int I, class C, class Ld>
+__device__ __forceinline__ void small_u_split(const C &coef, const Ld &ld, const int *vtx, double *sU, int nn,
+                                              int node, bool &bad)
+{
+    if constexpr (I < D) {
+        using S = Shape<D, M>;
+        double out[S::NQ];
+#pragma unroll
+        for (int s = 0; s < S::NQ; ++s) out[s] = sU[(I * S::NQ + s) * nn + node];
+        u_node<D, M, I, 1>(coef, ld, vtx, out);
+#pragma unroll
+        for (int s = 0; s < S::NQ; ++s) {
+            sU[(I * S::NQ + s) * nn + node] = out[s];
+            bad |= !isfinite(out[s]);
+        }
+        small_u_split<D, M, I + 1>(coef, ld, vtx, sU, nn, node, bad);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-CTA persistent kernel for tiny grids: the whole state lives in shared
+// memory and all n_steps run in one launch (no launch or grid-barrier cost).
+template <int D, int M, class C>
+__global__ void __launch_bounds__(256) k_small(double *__restrict__ P, double *__restrict__ U, GridDesc g, C coef,
+                                               int64_t nsteps, unsigned *status)
+{
+    using S = Shape<D, M>;
+    extern __shared__ double smem[];
+    const int nn = (int)g.nnode;
+    double *sP = smem;
+    double *sU = smem + (int64_t)S::NQ * nn;
+    for (int e = threadIdx.x; e < S::NQ * nn; e += blockDim.x) sP[e] = P[e];
+    for (int e = threadIdx.x; e < D * S::NQ * nn; e += blockDim.x) sU[e] = U[e];
+    __syncthreads();
+    bool bad = false;
+    SharedLd ldU{sU, nn, S::NQ};
+    SharedLd ldP{sP, nn, S::NQ};
+    for (int64_t st = 0; st < nsteps; ++st) {
+        for (int node = threadIdx.x; node < nn; node += blockDim.x) {
+            int vtx[S::NV];
+            vertex_nodes<D>(g, node, -1, vtx);
+            double out[S::NQ];
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) out[s] = sP[s * nn + node];
+            p_node<D, M>(coef, ldU, vtx, out);
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) {
+                sP[s * nn + node] = out[s];
+                bad |= !isfinite(out[s]);
+            }
+        }
+        __syncthreads();
+        for (int node = threadIdx.x; node < nn; node += blockDim.x) {
+            int vtx[S::NV];
+            vertex_nodes<D>(g, node, 0, vtx);
+            if constexpr (S::kUFused) {
+                double out[D * S::NQ];
+#pragma unroll
+                for (int e = 0; e < D * S::NQ; ++e) out[e] = sU[e * nn + node];
+                u_node<D, M, 0, D>(coef, ldP, vtx, out);
+#pragma unroll
+                for (int e = 0; e < D * S::NQ; ++e) {
+                    sU[e * nn + node] = out[e];
+                    bad |= !isfinite(out[e]);
+                }
+            } else {
+                small_u_split<D, M, 0>(coef, ldP, vtx, sU, nn, node, bad);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < S::NQ * nn; e += blockDim.x) P[e] = sP[e];
+    for (int e = threadIdx.x; e < D * S::NQ * nn; e += blockDim.x) U[e] = sU[e];
+    report_nonfinite(bad, status);
+}
+
+}  // namespace hl

@@ -1,0 +1,228 @@
+"""Thin Python binding of the C ABI in include/hl.h (libhl.so): argument marshalling only.
+
+Every call here forwards to the CUDA library of the same name; no step of the
+method runs in Python.  Host buffers are numpy float64 arrays (or CPU torch
+tensors); device buffers are CUDA torch tensors (anything with ``data_ptr()``).
+If libhl.so has not been built, loading fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhl.so")
+
+HL_OK, HL_EINVAL, HL_ENOMEM, HL_ECUDA, HL_ETIMEOUT, HL_ENONFINITE, HL_ESTATE = 0, -1, -2, -3, -4, -5, -6
+HL_FP64 = 0
+HL_OPT_KERNEL_PATH = 1
+HL_OPT_TIMING = 2
+CODE_NAMES = {0: "HL_OK", -1: "HL_EINVAL", -2: "HL_ENOMEM", -3: "HL_ECUDA", -4: "HL_ETIMEOUT",
+              -5: "HL_ENONFINITE", -6: "HL_ESTATE"}
+
+
+class HLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODE_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+# (name, restype, argtypes): mirrors include/hl.h
+_SIGNATURES = [
+    ("hl_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, ctypes.POINTER(_P)]),
+    ("hl_set_initial", ctypes.c_int, [_P, _P, _P]),
+    ("hl_set_initial_device", ctypes.c_int, [_P, _P, _P]),
+    ("hl_get_fields_device", ctypes.c_int, [_P, _P, _P]),
+    ("hl_step", ctypes.c_int, [_P, _I64]),
+    ("hl_get_fields", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("hl_sync", ctypes.c_int, [_P]),
+    ("hl_destroy", None, [_P]),
+    ("hl_last_error", ctypes.c_char_p, [_P]),
+    ("hl_set_stream", ctypes.c_int, [_P, _P]),
+    ("hl_bind_device", ctypes.c_int, [_P, _P, _P]),
+    ("hl_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
+    ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
+    ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("hl_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libhl.so (raises if it is missing: the library has no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhl.so not found at {path}; build it with paper_1808_10481_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Handle:
+    """Opaque solver pointer plus the sizes needed to marshal buffers."""
+    ptr: ctypes.c_void_p
+    dim: int
+    m: int
+    n_cells: tuple
+    dt: float
+
+    @property
+    def nnode(self) -> int:
+        return int(np.prod(self.n_cells))
+
+    @property
+    def nq(self) -> int:
+        return (self.m + 1) ** self.dim
+
+
+def _err(h) -> str:
+    return load().hl_last_error(h.ptr if isinstance(h, Handle) else h).decode(errors="replace")
+
+
+def _check(h, rc: int) -> int:
+    if rc != HL_OK:
+        raise HLError(rc, _err(h))
+    return rc
+
+
+def _host_ptr(a, count: int, writable: bool):
+    if hasattr(a, "data_ptr"):            # CPU torch tensor
+        if a.is_cuda:
+            raise ValueError("expected a host buffer")
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous() or a.numel() != count:
+            raise ValueError("host buffer must be contiguous float64 with the solver's size")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or a.size != count:
+        raise ValueError("host buffer must be a C-contiguous float64 numpy array with the solver's size")
+    if writable and not a.flags.writeable:
+        raise ValueError("host output buffer is read-only")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t, count: int):
+    if t is None:
+        return None
+    if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+        raise ValueError("expected a CUDA tensor")
+    if str(t.dtype) != "torch.float64" or not t.is_contiguous() or t.numel() != count:
+        raise ValueError("device buffer must be contiguous float64 with the solver's size")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------- entry points
+def hl_create(dim: int, m: int, n_cells, dt: float) -> Handle:
+    lib = load()
+    nc = (_I64 * len(n_cells))(*[int(x) for x in n_cells])
+    out = _P()
+    rc = lib.hl_create(int(dim), int(m), nc, float(dt), ctypes.byref(out))
+    if rc != HL_OK:
+        raise HLError(rc, lib.hl_last_error(None).decode(errors="replace"))
+    return Handle(out, int(dim), int(m), tuple(int(x) for x in n_cells), float(dt))
+
+
+def hl_set_initial(h: Handle, p, u) -> None:
+    n = h.nnode * h.nq
+    _check(h, load().hl_set_initial(h.ptr, _host_ptr(p, n, False), _host_ptr(u, n * h.dim, False)))
+
+
+def hl_set_initial_device(h: Handle, p_dev, u_dev) -> None:
+    n = h.nnode * h.nq
+    _check(h, load().hl_set_initial_device(h.ptr, _dev_ptr(p_dev, n), _dev_ptr(u_dev, n * h.dim)))
+
+
+def hl_get_fields_device(h: Handle, p_dev=None, u_dev=None) -> None:
+    n = h.nnode * h.nq
+    _check(h, load().hl_get_fields_device(h.ptr, _dev_ptr(p_dev, n), _dev_ptr(u_dev, n * h.dim)))
+
+
+def hl_step(h: Handle, n_steps: int) -> None:
+    _check(h, load().hl_step(h.ptr, int(n_steps)))
+
+
+def hl_get_fields(h: Handle, p=None, u=None, raise_nonfinite: bool = True):
+    """Copy the state to host arrays (allocated if None); returns (p, u, t_p, t_u)."""
+    n = h.nnode * h.nq
+    if p is None:
+        p = np.empty((h.nnode, h.nq), dtype=np.float64)
+    if u is None:
+        u = np.empty((h.dim, h.nnode, h.nq), dtype=np.float64)
+    tp, tu = _D(), _D()
+    rc = load().hl_get_fields(h.ptr, _host_ptr(p, n, True), _host_ptr(u, n * h.dim, True),
+                              ctypes.byref(tp), ctypes.byref(tu))
+    if rc != HL_OK and (rc != HL_ENONFINITE or raise_nonfinite):
+        raise HLError(rc, _err(h))
+    return p, u, tp.value, tu.value
+
+
+def hl_sync(h: Handle) -> int:
+    """Returns HL_OK or HL_ENONFINITE; raises on CUDA failure."""
+    rc = load().hl_sync(h.ptr)
+    if rc not in (HL_OK, HL_ENONFINITE):
+        raise HLError(rc, _err(h))
+    return rc
+
+
+def hl_destroy(h: Handle) -> None:
+    if h is not None and h.ptr:
+        load().hl_destroy(h.ptr)
+        h.ptr = _P()
+
+
+def hl_last_error(h: Handle | None) -> str:
+    return load().hl_last_error(h.ptr if h is not None else None).decode(errors="replace")
+
+
+def hl_set_stream(h: Handle, stream) -> None:
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(h, load().hl_set_stream(h.ptr, ctypes.c_void_p(int(raw) if raw else 0)))
+
+
+def hl_bind_device(h: Handle, p_dev, u_dev) -> None:
+    n = h.nnode * h.nq
+    _check(h, load().hl_bind_device(h.ptr, _dev_ptr(p_dev, n), _dev_ptr(u_dev, n * h.dim)))
+
+
+def hl_set_precision(h: Handle, mode: int) -> None:
+    _check(h, load().hl_set_precision(h.ptr, int(mode)))
+
+
+def hl_set_option(h: Handle, option: int, value: int) -> None:
+    _check(h, load().hl_set_option(h.ptr, int(option), int(value)))
+
+
+def hl_kernel_times(h: Handle):
+    """Returns ({'p_half','u_half','small'}: total ms, same keys: launch counts) and resets."""
+    ms = (_D * 3)()
+    n = (_I64 * 3)()
+    _check(h, load().hl_kernel_times(h.ptr, ms, n))
+    keys = ("p_half", "u_half", "small")
+    return dict(zip(keys, list(ms))), dict(zip(keys, list(n)))
+
+
+def hl_op_counts(dim: int, m: int):
+    f, a = _D(), _D()
+    rc = load().hl_op_counts(int(dim), int(m), ctypes.byref(f), ctypes.byref(a))
+    if rc != HL_OK:
+        raise HLError(rc, hl_last_error(None))
+    return f.value, a.value
+
+
+def hl_info(h: Handle):
+    nn, nq, st = _I64(), _I64(), _I64()
+    _check(h, load().hl_info(h.ptr, ctypes.byref(nn), ctypes.byref(nq), ctypes.byref(st)))
+    return nn.value, nq.value, st.value

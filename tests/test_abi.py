@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and exports
+every entry point include/hl.h declares, the binding wraps each of them, argument
+validation happens before any CUDA call, and the kernels' compile-time sparsity
+rule matches the true operator (computed here from the oracle on unit inputs)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_10481_gb300 import build as B
+from paper_1808_10481_gb300 import hl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "hl.h")).read()
+    return re.findall(r"^\s*(?:int|void|const char)\s*\*?\s*(hl_\w+)\s*\(", txt, re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ctypes.CDLL(B.LIB)
+
+
+def test_header_declares_the_core_entry_points():
+    names = set(_declared())
+    for n in ["hl_create", "hl_set_initial", "hl_step", "hl_get_fields", "hl_destroy", "hl_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_wraps_every_declared_symbol():
+    for name in _declared():
+        assert callable(getattr(hl, name, None)), name
+
+
+@pytest.mark.parametrize("args,fragment", [
+    ((0, 3, [8], 0.01), "dim"),
+    ((4, 3, [8], 0.01), "dim"),
+    ((2, -1, [8, 8], 0.01), "m must"),
+    ((2, 7, [8, 8], 0.01), "m must"),
+    ((3, 4, [8, 8, 8], 0.01), "m <= 3"),
+    ((2, 3, [1, 8], 0.01), ">= 2"),
+    ((2, 3, [8, 8], 0.0), "dt"),
+    ((2, 3, [8, 8], float("nan")), "dt"),
+    ((2, 3, [8, 16], 0.07), "min h"),
+    ((3, 1, [2048, 2048, 1024], 1e-5), "2^31"),
+])
+def test_invalid_arguments_rejected_before_cuda(args, fragment):
+    hl.load()
+    with pytest.raises(hl.HLError) as ei:
+        hl.hl_create(*args)
+    assert ei.value.code == hl.HL_EINVAL
+    assert fragment in str(ei.value)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    lib.hl_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.hl_step(None, 1) == hl.HL_EINVAL
+    lib.hl_destroy.argtypes = [ctypes.c_void_p]
+    lib.hl_destroy(None)
+
+
+def _butterflied_nnz(d, m, lam):
+    """Non-zeros of the all-lower-vertex operator block, from the oracle's node update
+    applied to unit vertex data (an independent route to the operator)."""
+    nq = (m + 1) ** d
+    nz = 0
+    for i in range(d):
+        for l in range(nq):
+            vtx = np.zeros((d, 1 << d, nq))
+            vtx[i, 0, l] = 1.0
+            col = oracle.node_update(d, m, lam, 0, vtx)[0]
+            nz += int(np.sum(np.abs(col) > 1e-13))
+    return nz
+
+
+@pytest.mark.parametrize("d,m", [(1, 3), (2, 2), (2, 3), (3, 1), (3, 2)])
+def test_kernel_sparsity_rule_matches_operator(d, m):
+    hl.load()
+    fma, add = hl.hl_op_counts(d, m)
+    nz = _butterflied_nnz(d, m, [0.45, 0.37, 0.29][:d])
+    assert fma == 2 * nz                       # p-half and u-half use the same table
+    assert add == d * (1 << d) * (m + 1) ** d * (d + 1)

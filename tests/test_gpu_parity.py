@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (stated in the workload definition): per field, max |gpu - oracle| / max |oracle|
+<= 1e-12 after the run, FP64 throughout.  Summation order differs between the two
+(butterflied fused operator vs. per-axis reconstruction + series), so results agree to
+rounding, not bitwise.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_10481_gb300 import hl
+from paper_1808_10481_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1808_10481_gb300 import build
+    build.build()
+    hl.load()
+
+
+def rel_err(got, ref):
+    scale = float(np.abs(ref).max())
+    return float(np.abs(np.asarray(got) - np.asarray(ref)).max()) / (scale if scale > 0 else 1.0)
+
+
+def gpu_run(d, m, ncell, dt, p, u, steps, path=0):
+    h = hl.hl_create(d, m, ncell, dt)
+    try:
+        if path:
+            hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, path)
+        hl.hl_set_initial(h, np.ascontiguousarray(p), np.ascontiguousarray(u))
+        hl.hl_step(h, steps)
+        pg, ug, tp, tu = hl.hl_get_fields(h)
+        assert math.isclose(tp, steps * dt) and math.isclose(tu, (steps + 0.5) * dt)
+        return pg, ug
+    finally:
+        hl.hl_destroy(h)
+
+
+SMALL_CASES = (
+    [(1, m, [n]) for m in range(7) for n in (2, 3, 7, 64)]
+    + [(2, m, nc) for m in range(5) for nc in ([2, 2], [3, 5], [17, 13])]
+    + [(2, 6, [5, 4])]
+    + [(3, m, nc) for m in range(4) for nc in ([2, 2, 2], [3, 4, 5])]
+    + [(3, 2, [9, 7, 5])]
+)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("d,m,ncell", SMALL_CASES)
+def test_random_state_parity(d, m, ncell, path):
+    """Random node data (every slot exercised), both kernel paths, tiny and odd grids
+    where periodic neighbours alias (n = 2, 3)."""
+    if path == 1 and (d + 1) * (m + 1) ** d * int(np.prod(ncell)) * 8 > 200 * 1024:
+        pytest.skip("state does not fit the single-CTA path")
+    dt = I.cfl_dt(ncell, 0.9)
+    st = I.random_state(d, m, ncell, seed=17 + m)
+    steps = 5
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, steps)
+    pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, steps, path)
+    assert rel_err(pg, po) <= TOL
+    assert rel_err(ug, uo) <= TOL
+
+
+def test_config1_full_1d_standing_mode():
+    """1D, 64 nodes, m = 3, p = sin(2 pi 3 x), 1000 steps at C_CFL = 0.9: full-run parity,
+    and the GPU error against the exact solution is at the oracle's level."""
+    d, m, ncell = 1, 3, [64]
+    dt = I.cfl_dt(ncell)
+    st = I.standing_mode(d, m, ncell, dt, wave=[3])
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 1000)
+    pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 1000)
+    assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
+    ex = I.standing_mode_exact(d, m, ncell, [3], 1000 * dt, 1000.5 * dt)
+    assert I.l2_error(d, ncell, pg, ex.p) < 1e-6
+
+
+@pytest.mark.parametrize("path", [0, 2])
+def test_config2_reduced_full_run(path):
+    """2D m = 3 Gaussian pulse (width 0.05) on 64^2 for the workload's 200 steps."""
+    d, m, ncell = 2, 3, [64, 64]
+    dt = I.cfl_dt(ncell)
+    st = I.gaussian_pulse(d, m, ncell, dt, seed=1)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 200)
+    pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 200, path)
+    assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
+
+
+def test_config3_reduced_full_run():
+    """3D m = 2 plane wave on 12^3 (ragged against the 128-thread blocks), 40 steps."""
+    d, m, ncell = 3, 2, [12, 12, 12]
+    dt = I.cfl_dt(ncell)
+    st = I.plane_wave(m, ncell, dt, seed=3)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 40)
+    pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 40)
+    assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
+
+
+def _sampled_step_parity(d, m, ncell, dt, st, warm_steps, n_sample, seed):
+    """At full size: run warm_steps on the GPU, read the state, do one more step on the
+    GPU and compare sampled nodes with the oracle's half-steps from the GPU state."""
+    h = hl.hl_create(d, m, ncell, dt)
+    try:
+        hl.hl_set_initial(h, st.p, st.u)
+        hl.hl_step(h, warm_steps)
+        p0, u0, _, _ = hl.hl_get_fields(h)
+        hl.hl_step(h, 1)
+        p1, u1, _, _ = hl.hl_get_fields(h)
+    finally:
+        hl.hl_destroy(h)
+    rng = np.random.default_rng(seed)
+    nnode = int(np.prod(ncell))
+    nodes = np.unique(np.concatenate([rng.choice(nnode, n_sample, replace=False), [0, nnode - 1]]))
+    p_half = oracle.half_step_nodes(d, m, ncell, dt, 0, u0, p0, nodes)[0]
+    assert rel_err(p1[nodes], p_half) <= TOL
+    # the u-half of the oracle from the GPU's new p
+    u_half = oracle.half_step_nodes(d, m, ncell, dt, 1, p1, u0, nodes)
+    assert rel_err(u1[:, nodes], u_half) <= TOL
+
+
+def test_config2_full_size_sampled():
+    """512^2, m = 3: the workload and launch configuration the benchmark times."""
+    d, m, ncell = 2, 3, [512, 512]
+    dt = I.cfl_dt(ncell)
+    _sampled_step_parity(d, m, ncell, dt, I.gaussian_pulse(d, m, ncell, dt, seed=1), 20, 4000, 5)
+
+
+def test_config3_full_size_sampled():
+    """256^3, m = 2 plane wave: 14.5 GB of FP64 state, sampled one-step parity."""
+    d, m, ncell = 3, 2, [256, 256, 256]
+    dt = I.cfl_dt(ncell)
+    _sampled_step_parity(d, m, ncell, dt, I.plane_wave(m, ncell, dt, seed=3), 2, 1500, 6)
+
+
+def test_zero_steps_is_identity_and_roundtrip_exact():
+    d, m, ncell = 2, 3, [7, 9]
+    st = I.random_state(d, m, ncell, seed=2)
+    pg, ug = gpu_run(d, m, ncell, I.cfl_dt(ncell), st.p, st.u, 0)
+    np.testing.assert_array_equal(pg, st.p)
+    np.testing.assert_array_equal(ug, st.u)
+
+
+def test_checkpoint_resume_is_bitwise():
+    d, m, ncell = 2, 3, [40, 24]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=4)
+    pa, ua = gpu_run(d, m, ncell, dt, st.p, st.u, 30)
+    pb, ub = gpu_run(d, m, ncell, dt, st.p, st.u, 12)
+    pc, uc = gpu_run(d, m, ncell, dt, pb, ub, 18)
+    np.testing.assert_array_equal(pa, pc)
+    np.testing.assert_array_equal(ua, uc)
+
+
+def test_deterministic():
+    d, m, ncell = 3, 2, [10, 9, 8]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=8)
+    a = gpu_run(d, m, ncell, dt, st.p, st.u, 7)
+    b = gpu_run(d, m, ncell, dt, st.p, st.u, 7)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_nonfinite_is_reported():
+    """Fault injection on the host: a NaN in the initial data must surface as
+    HL_ENONFINITE after stepping (no GPU fault involved)."""
+    d, m, ncell = 2, 2, [16, 16]
+    st = I.random_state(d, m, ncell, seed=1)
+    st.u[0, 5, 3] = np.nan
+    h = hl.hl_create(d, m, ncell, I.cfl_dt(ncell))
+    try:
+        hl.hl_set_initial(h, st.p, st.u)
+        hl.hl_step(h, 1)
+        assert hl.hl_sync(h) == hl.HL_ENONFINITE
+        assert hl.hl_sync(h) == hl.HL_OK          # the flag is cleared once read
+        with pytest.raises(hl.HLError) as ei:
+            hl.hl_step(h, 1)
+            hl.hl_get_fields(h)
+        assert ei.value.code == hl.HL_ENONFINITE
+    finally:
+        hl.hl_destroy(h)
+
+
+def test_torch_stream_and_bound_device_buffers():
+    """PyTorch owns the device memory and the stream; the library works in place."""
+    torch = pytest.importorskip("torch")
+    d, m, ncell = 2, 3, [33, 20]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=6)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 6)
+    dev = torch.device("cuda:0")
+    # device layout is slot-major: p[q][node], u[comp][q][node]
+    p_dev = torch.from_numpy(np.ascontiguousarray(st.p.T)).to(dev)
+    u_dev = torch.from_numpy(np.ascontiguousarray(st.u.transpose(0, 2, 1))).to(dev)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()                    # the uploads above ran on torch's stream
+    h = hl.hl_create(d, m, ncell, dt)
+    try:
+        hl.hl_set_stream(h, s)
+        hl.hl_bind_device(h, p_dev, u_dev)
+        hl.hl_step(h, 6)
+        assert hl.hl_sync(h) == hl.HL_OK
+        pg = p_dev.cpu().numpy().T
+        ug = u_dev.cpu().numpy().transpose(0, 2, 1)
+        assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
+        # host-layout device copies
+        p_aos = torch.empty((st.p.shape[0], st.p.shape[1]), dtype=torch.float64, device=dev)
+        u_aos = torch.empty(st.u.shape, dtype=torch.float64, device=dev)
+        hl.hl_get_fields_device(h, p_aos, u_aos)
+        assert hl.hl_sync(h) == hl.HL_OK
+        np.testing.assert_array_equal(p_aos.cpu().numpy(), pg)
+        np.testing.assert_array_equal(u_aos.cpu().numpy(), ug)
+    finally:
+        hl.hl_destroy(h)

@@ -375,3 +375,20 @@ def test_2d_convergence_rate_matches_table5(m):
     # the paper's [-1,1]^2 mode sin(pi x) sin(pi y) cos(sqrt(2) pi t) mapped to [0,1]^2
     got = _rate(2, m, [8, 12, 16, 24, 32], T=0.5, wave=[1, 1])
     _check_rate(m, got, paper)
+
+
+def test_half_step_nodes_matches_full_half_step():
+    """The sampled-node entry point is the full half-step restricted to those nodes."""
+    rng = np.random.default_rng(11)
+    for d, m, ncell in [(1, 3, [9]), (2, 2, [5, 7]), (3, 1, [3, 4, 5])]:
+        st = I.random_state(d, m, ncell, seed=5)
+        nodes = rng.choice(int(np.prod(ncell)), size=6, replace=False)
+        for mode in (0, 1):
+            src, dst = (st.u, st.p) if mode == 0 else (st.p, st.u)
+            full = np.array(dst, copy=True)
+            oracle.half_step(d, m, ncell, 0.3 / max(ncell), mode, np.ascontiguousarray(src), full)
+            got = oracle.half_step_nodes(d, m, ncell, 0.3 / max(ncell), mode, src, dst, nodes)
+            full = full.reshape(-1 if mode == 0 else d, int(np.prod(ncell)), (m + 1) ** d)
+            if mode == 0:
+                full = full.reshape(1, int(np.prod(ncell)), (m + 1) ** d)
+            np.testing.assert_array_equal(got, full[:, nodes, :])
