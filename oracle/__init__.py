@@ -60,6 +60,13 @@ def _load():
     lib.oracle_half_step_nodes.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, ctypes.c_int, dp, dp,
                                             i64p, ctypes.c_int64, dp]
     lib.oracle_half_step_nodes.restype = None
+    lib.oracle_add_source.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    lib.oracle_add_source.restype = None
+    lib.oracle_run_source.argtypes = [ctypes.c_int, ctypes.c_int, i64p, dp, dp, ctypes.c_double, dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, dp, dp,
+                                       ctypes.c_int64]
+    lib.oracle_run_source.restype = None
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_threads.restype = ctypes.c_int
     _lib = lib
@@ -151,7 +158,38 @@ def run(d: int, m: int, ncell, dt: float, p: np.ndarray, u: np.ndarray, n_steps:
     return p, u
 
 
-__all__ = [
+def _nc(ncell):
+    return np.array(list(ncell) + [1] * (3 - len(ncell)), dtype=np.int64)
+
+
+def add_source(d: int, m: int, ncell, x0, sigma: float, f0: float, amp: float, t_mid: float, dt: float,
+               p: np.ndarray) -> None:
+    """p~ += dt * amp * R(t_mid) * g~ in place (Ricker wavelet times a Gaussian, midpoint rule)."""
+    lib = _load()
+    assert p.dtype == np.float64 and p.flags.c_contiguous
+    x = np.zeros(3)
+    x[:d] = np.asarray(x0, dtype=np.float64)[:d]
+    nc = _nc(ncell)
+    lib.oracle_add_source(d, m, nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(x), float(sigma),
+                          float(f0), float(amp), float(t_mid), float(dt), _dptr(p))
+
+
+def run_source(d: int, m: int, ncell, dt: float, p, u, n_steps: int, x0, sigma: float, f0: float, amp: float,
+               step0: int = 0):
+    """run() with the point source injected after every p-half; returns new (p, u)."""
+    lib = _load()
+    p = np.array(p, dtype=np.float64, order="C", copy=True)
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    x = np.zeros(3)
+    x[:d] = np.asarray(x0, dtype=np.float64)[:d]
+    nc = _nc(ncell)
+    lib.oracle_run_source(d, m, nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(lambdas(ncell, dt)),
+                          _dptr(_h_array(m)), float(dt), _dptr(x), float(sigma), float(f0), float(amp),
+                          int(step0), _dptr(p), _dptr(u), int(n_steps))
+    return p, u
+
+
+__all__ = ["add_source", "run_source",
     "build", "node_update", "half_step", "half_step_nodes", "run", "lambdas", "set_threads", "threads",
     "hermite_inverse", "hermite_inverse_exact", "interp_system",
 ]

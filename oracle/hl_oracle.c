@@ -286,6 +286,84 @@ void oracle_run(int d, int m, const int64_t *ncell, const double *lam, const dou
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Point source (not in the paper; the workload's Ricker source).  The paper's
+ * forced experiments add a source z(x,t) to the pressure equation (Section 4,
+ * eq. waveEq1D) without stating its time discretisation; here the source
+ *     f(x,t) = amp * R(t) * g(x),
+ *     R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),  t0 = 1.2/f0,
+ *     g(x) = exp(-|x - x0|^2 / (2 sigma^2))   (nearest periodic image),
+ * enters the p-half by the midpoint rule: p~_a += dt * amp * R(t_n + dt/2) * g~_a,
+ * with g~_a the exact scaled derivatives prod_k h_k^{a_k}/a_k! d^{a_k} g_k. */
+static double orc_ricker(double t, double f0)
+{
+    const double pi = 3.14159265358979323846;
+    const double t0 = 1.2 / f0;
+    const double arg = pi * pi * f0 * f0 * (t - t0) * (t - t0);
+    return (1.0 - 2.0 * arg) * exp(-arg);
+}
+
+/* scaled derivatives (h^a/a!) d^a/dx^a exp(-z^2/2), z = (x - c)/sigma, a = 0..m:
+ * d^a exp(-z^2/2)/dx^a = (-1/sigma)^a He_a(z) exp(-z^2/2) (probabilists' Hermite). */
+static void orc_gauss_1d(double dx, double sigma, double h, int m, double *out)
+{
+    const double z = dx / sigma;
+    const double g = exp(-0.5 * z * z);
+    double he_prev = 1.0, he = z;
+    for (int a = 0; a <= m; ++a) {
+        double hea = a == 0 ? 1.0 : (a == 1 ? z : 0.0);
+        if (a >= 2) {
+            double next = z * he - (double)(a - 1) * he_prev;
+            he_prev = he;
+            he = next;
+            hea = he;
+        }
+        out[a] = pow(-h / sigma, (double)a) / orc_fact(a) * hea * g;
+    }
+}
+
+void oracle_add_source(int d, int m, const int64_t *ncell, const double *x0, double sigma, double f0,
+                       double amp, double t_mid, double dt, double *p)
+{
+    const int n = m + 1;
+    const int64_t nq = ipow(n, d);
+    int64_t N[ORC_MAXD] = {1, 1, 1};
+    int64_t nnode = 1;
+    for (int k = 0; k < d; ++k) { N[k] = ncell[k]; nnode *= N[k]; }
+    const double w = dt * amp * orc_ricker(t_mid, f0);
+#pragma omp parallel for schedule(static)
+    for (int64_t node = 0; node < nnode; ++node) {
+        double fac[ORC_MAXD][ORC_MAXM + 1];
+        int64_t t = node;
+        for (int k = 0; k < d; ++k) {
+            const int64_t j = t % N[k];
+            t /= N[k];
+            const double h = 1.0 / (double)N[k];
+            double dx = (double)j * h - x0[k];
+            dx -= floor(dx + 0.5);          /* nearest periodic image */
+            orc_gauss_1d(dx, sigma, h, m, fac[k]);
+        }
+        for (int64_t q = 0; q < nq; ++q) {
+            double g = 1.0;
+            int64_t qq = q;
+            for (int k = 0; k < d; ++k) { g *= fac[k][qq % n]; qq /= n; }
+            p[node * nq + q] += w * g;
+        }
+    }
+}
+
+/* n_steps steps with the point source added after each p-half. */
+void oracle_run_source(int d, int m, const int64_t *ncell, const double *lam, const double *H, double dt,
+                       const double *x0, double sigma, double f0, double amp, int64_t step0,
+                       double *p, double *u, int64_t n_steps)
+{
+    for (int64_t s = 0; s < n_steps; ++s) {
+        oracle_half_step(d, m, ncell, lam, H, 0, u, p);
+        oracle_add_source(d, m, ncell, x0, sigma, f0, amp, ((double)(step0 + s) + 0.5) * dt, dt, p);
+        oracle_half_step(d, m, ncell, lam, H, 1, p, u);
+    }
+}
+
 void oracle_set_threads(int n)
 {
 #ifdef _OPENMP

@@ -40,6 +40,10 @@ struct hl_solver {
     size_t ev_used = 0;
     double t_p_ms = 0.0, t_u_ms = 0.0, t_small_ms = 0.0;
     int64_t n_p = 0, n_u = 0, n_small = 0;
+    // point source
+    SourceDesc src;
+    int *src_nodes = nullptr;
+    double *src_table = nullptr;
 };
 
 static thread_local std::string g_create_error;
@@ -78,6 +82,8 @@ static void release(hl_solver *h)
 {
     if (!h) return;
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->src_nodes) cudaFree(h->src_nodes);
+    if (h->src_table) cudaFree(h->src_table);
     if (h->p_own) cudaFree(h->p_own);
     if (h->u_own) cudaFree(h->u_own);
     if (h->staging) cudaFree(h->staging);
@@ -351,6 +357,8 @@ extern "C" int hl_step(hl_solver *h, int64_t n_steps)
     a.stream = h->stream;
     a.status = h->status;
     a.path = h->path;
+    a.src = h->src;
+    a.step0 = h->steps;
     a.ev = nullptr;
     bool used_small = false;
     a.used_small = &used_small;
@@ -377,6 +385,49 @@ extern "C" int hl_step(hl_solver *h, int64_t n_steps)
         h->ev_used = first + (used_small ? 2 : 2 * (size_t)n_steps + 1);
     }
     h->steps += n_steps;
+    return HL_OK;
+}
+
+extern "C" int hl_set_source(hl_solver *h, const double *x0, double sigma, double f0, double amp)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (amp == 0.0) {
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        if (h->src_nodes) cudaFree(h->src_nodes);
+        if (h->src_table) cudaFree(h->src_table);
+        h->src_nodes = nullptr;
+        h->src_table = nullptr;
+        h->src = SourceDesc();
+        return HL_OK;
+    }
+    if (!x0) return set_err(h, HL_EINVAL, "x0 is NULL");
+    for (int k = 0; k < h->dim; ++k)
+        if (!std::isfinite(x0[k])) return set_err(h, HL_EINVAL, "x0 must be finite");
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return set_err(h, HL_EINVAL, "sigma must be finite and > 0");
+    if (!(f0 > 0.0) || !std::isfinite(f0)) return set_err(h, HL_EINVAL, "f0 must be finite and > 0");
+    if (!std::isfinite(amp)) return set_err(h, HL_EINVAL, "amp must be finite");
+    std::vector<int> nodes;
+    std::vector<double> table;
+    if (!build_source_table(h->dim, h->m, h->n, x0, sigma, nodes, table))
+        return set_err(h, HL_EINVAL, "source box too large");
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->src_nodes) cudaFree(h->src_nodes);
+    if (h->src_table) cudaFree(h->src_table);
+    h->src_nodes = nullptr;
+    h->src_table = nullptr;
+    h->src = SourceDesc();
+    HL_CK(h, cudaMalloc(&h->src_nodes, nodes.size() * sizeof(int)));
+    HL_CK(h, cudaMalloc(&h->src_table, table.size() * sizeof(double)));
+    HL_CK(h, cudaMemcpy(h->src_nodes, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HL_CK(h, cudaMemcpy(h->src_table, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h->src.active = true;
+    h->src.nb = (int)nodes.size();
+    h->src.nodes = h->src_nodes;
+    h->src.table = h->src_table;
+    h->src.dt = h->dt;
+    h->src.amp = amp;
+    h->src.f0 = f0;
     return HL_OK;
 }
 

@@ -25,6 +25,7 @@ static bool use_small(const LaunchFp64 &a)
     using S = Shape<D, M>;
     const size_t smem = (size_t)(D + 1) * S::NQ * a.nnode * sizeof(double);
     if (smem > 200 * 1024) return false;
+    if (a.src.active) return false;  // the source is injected between launches
     if (a.path == PATH_SMALL) return true;
     if (a.path == PATH_GRID) return false;
     return (double)a.nnode * S::NQ * S::NQ * D <= 40000.0;
@@ -59,6 +60,10 @@ static cudaError_t run_fp64(const LaunchFp64 &a)
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
         k_p_half<D, M, C><<<blocks, 128, 0, a.stream>>>(a.U, a.P, g, coef, a.status);
+        if (a.src.active) {
+            cudaError_t e = launch_source(a.src, a.P, a.nnode, S::NQ, a.step0 + st, a.stream);
+            if (e != cudaSuccess) return e;
+        }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
         if constexpr (S::kUFused)
             k_u_half<D, M, 0, D, C><<<blocks, 128, 0, a.stream>>>(a.P, a.U, g, coef, a.status);

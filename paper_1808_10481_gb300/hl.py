@@ -48,6 +48,7 @@ _SIGNATURES = [
     ("hl_last_error", ctypes.c_char_p, [_P]),
     ("hl_set_stream", ctypes.c_int, [_P, _P]),
     ("hl_bind_device", ctypes.c_int, [_P, _P, _P]),
+    ("hl_set_source", ctypes.c_int, [_P, ctypes.POINTER(_D), _D, _D, _D]),
     ("hl_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
@@ -195,6 +196,11 @@ def hl_set_stream(h: Handle, stream) -> None:
 def hl_bind_device(h: Handle, p_dev, u_dev) -> None:
     n = h.nnode * h.nq
     _check(h, load().hl_bind_device(h.ptr, _dev_ptr(p_dev, n), _dev_ptr(u_dev, n * h.dim)))
+
+
+def hl_set_source(h: Handle, x0, sigma: float, f0: float, amp: float) -> None:
+    x = (_D * 3)(*([float(v) for v in x0] + [0.0] * (3 - len(x0))))
+    _check(h, load().hl_set_source(h.ptr, x, float(sigma), float(f0), float(amp)))
 
 
 def hl_set_precision(h: Handle, mode: int) -> None:

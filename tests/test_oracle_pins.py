@@ -392,3 +392,55 @@ def test_half_step_nodes_matches_full_half_step():
             if mode == 0:
                 full = full.reshape(1, int(np.prod(ncell)), (m + 1) ** d)
             np.testing.assert_array_equal(got, full[:, nodes, :])
+
+
+# ----------------------------------------------------------------------------- point source
+def test_source_spatial_factor_matches_symbolic_derivatives():
+    """g~_a = prod_k h^{a_k}/a_k! d^{a_k} exp(-(x_k - x0_k)^2 / (2 sigma^2)), checked against
+    sympy's symbolic derivatives; R(t0) = 1 isolates the spatial factor."""
+    sp = pytest.importorskip("sympy")
+    d, m, ncell = 2, 3, [40, 32]
+    x0 = [0.512, 0.47]
+    sigma, f0 = 0.03, 12.0
+    p = np.zeros((int(np.prod(ncell)), (m + 1) ** d))
+    oracle.add_source(d, m, ncell, x0, sigma, f0, amp=1.0, t_mid=1.2 / f0, dt=1.0, p=p)
+    X = sp.Symbol("x")
+    derivs = []
+    for k in range(d):
+        g = sp.exp(-(X - sp.Rational(str(x0[k]))) ** 2 / (2 * sp.Rational(str(sigma)) ** 2))
+        derivs.append([sp.lambdify(X, sp.diff(g, X, a)) for a in range(m + 1)])
+    for node in [0, 20 + 40 * 15, 21 + 40 * 14, 25 + 40 * 18]:
+        j = [node % ncell[0], node // ncell[0]]
+        for q in range((m + 1) ** d):
+            a = [q % (m + 1), q // (m + 1)]
+            want = 1.0
+            for k in range(d):
+                h = 1.0 / ncell[k]
+                want *= h ** a[k] / math.factorial(a[k]) * float(derivs[k][a[k]](j[k] * h))
+            assert abs(p[node, q] - want) <= 1e-13 * max(1.0, abs(want))
+
+
+def test_ricker_wavelet_closed_form_points():
+    """R(t0) = 1 and R vanishes at t0 +- 1/(sqrt(2) pi f0), read through a one-node-sized
+    source: with x0 on a node, g~_0 = 1 there."""
+    d, m, ncell = 1, 0, [16]
+    f0 = 15.0
+    t0 = 1.2 / f0
+    for t, want in [(t0, 1.0), (t0 + 1.0 / (math.sqrt(2.0) * math.pi * f0), 0.0),
+                    (t0 - 1.0 / (math.sqrt(2.0) * math.pi * f0), 0.0)]:
+        p = np.zeros((16, 1))
+        oracle.add_source(d, m, ncell, [0.25], 0.01, f0, amp=1.0, t_mid=t, dt=1.0, p=p)
+        assert abs(p[4, 0] - want) <= 1e-14
+
+
+def test_source_superposition():
+    """The forced scheme is linear: run with source = run without + forced run from rest."""
+    d, m, ncell = 2, 2, [24, 20]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=21)
+    args = dict(x0=[0.4, 0.6], sigma=0.05, f0=10.0, amp=3.0)
+    pf, uf = oracle.run_source(d, m, ncell, dt, st.p, st.u, 12, **args)
+    p0, u0 = oracle.run(d, m, ncell, dt, st.p, st.u, 12)
+    ps, us = oracle.run_source(d, m, ncell, dt, np.zeros_like(st.p), np.zeros_like(st.u), 12, **args)
+    np.testing.assert_allclose(pf, p0 + ps, rtol=0, atol=1e-12 * np.abs(pf).max())
+    np.testing.assert_allclose(uf, u0 + us, rtol=0, atol=1e-12 * np.abs(uf).max())
