@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hl", "reference"], default="hl")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["2d", "1d", "3d", "batch"], default="2d",
+                    help="2d: the headline line; the others measure further rows of the solver")
     return ap.parse_args()
 
 
@@ -177,6 +179,93 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def fp64_flops_per_node_step(dim, m):
+    """Algorithmic FP64 flops of one node and full step of the fused kernels
+    (multiply-add = 2, butterfly and final additions = 1)."""
+    from paper_1808_10481_gb300 import hl
+    fma, add = hl.hl_op_counts(dim, m)
+    return 2 * fma + add
+
+
+def run_aux(args):
+    """Single-GPU measurements of the other workloads (one JSON line each)."""
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import build as libbuild
+    from paper_1808_10481_gb300 import hl
+    from paper_1808_10481_gb300 import inputs as I
+
+    libbuild.build()
+    hl.load()
+    stream = torch.cuda.current_stream()
+    out = {"metric": METRIC, "unit": UNIT, "dtype": "f64", "data": "synthetic", "higher_is_better": True}
+    if args.workload in ("1d", "3d"):
+        if args.workload == "1d":
+            d, m, ncell, lf = 1, 3, [64], 1000
+            dt = I.cfl_dt(ncell)
+            st = I.standing_mode(d, m, ncell, dt, wave=[3])
+            desc = "1D, 64 nodes, m=3, p=sin(2 pi 3 x), u at dt/2 from the exact standing mode, 1000 steps"
+        else:
+            d, m, ncell, lf = 3, 2, [256, 256, 256], 100
+            dt = I.cfl_dt(ncell)
+            st = I.plane_wave(m, ncell, dt, seed=3)
+            desc = "3D, 256^3 nodes per grid, m=2, plane wave |n|<=8 (seed 3), 100 steps"
+        h = hl.hl_create(d, m, ncell, dt)
+        hl.hl_set_stream(h, stream)
+        hl.hl_set_initial(h, st.p, st.u)
+        hl.hl_step(h, min(lf, 3))
+        hl.hl_sync(h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hl.hl_step(h, lf)
+        e1.record(stream)
+        rc = hl.hl_sync(h)
+        ms = e0.elapsed_time(e1)
+        hl.hl_destroy(h)
+        nnode = int(np.prod(ncell))
+        dof = (d + 1) * (m + 1) ** d * nnode
+        fl = fp64_flops_per_node_step(d, m) * nnode * lf
+        out.update({"workload": args.workload, "value": dof * lf / (ms / 1e3), "ms_per_run": ms,
+                    "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
+                    "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                                 "unit": "TFLOP/s", "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS},
+                    "status": rc})
+    else:
+        d, m, n_shots, lf = 2, 3, 64, 500
+        rng = np.random.default_rng(2024)
+        sizes = [int(x) for x in rng.integers(128, 1025, size=n_shots)]
+        cells = [[n, n] for n in sizes]
+        dts = [I.cfl_dt(c) for c in cells]
+        x0 = [list(rng.random(2)) for _ in range(n_shots)]
+        f0 = [float(x) for x in rng.uniform(10.0, 20.0, size=n_shots)]
+        h = hl.hl_create_batch(d, m, cells, dts)
+        hl.hl_set_stream(h, stream)
+        best, tile_ms = hl.hl_autotune(h, 2)
+        hl.hl_set_sources(h, x0, [0.01] * n_shots, f0, [1.0] * n_shots)
+        hl.hl_step(h, 5)
+        hl.hl_sync(h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hl.hl_step(h, lf)
+        e1.record(stream)
+        rc = hl.hl_sync(h)
+        ms = e0.elapsed_time(e1)
+        hl.hl_destroy(h)
+        nnode = sum(n * n for n in sizes)
+        dof = (d + 1) * (m + 1) ** d * nnode
+        fl = fp64_flops_per_node_step(d, m) * nnode * lf
+        out.update({"workload": "batch", "value": dof * lf / (ms / 1e3), "ms_per_run": ms,
+                    "config": {"workload": "64 independent 2D shots, n ~ U{128..1024} per axis (seed 2024), m=3, "
+                                           "FP64, Ricker source per shot (f0 ~ U[10,20], sigma 0.01, seeded x0) "
+                                           "from a zero field, 500 steps, one CUDA graph per run",
+                               "total_nodes": nnode, "tile": hl.TILES[best], "tile_ms_per_step": tile_ms},
+                    "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                                 "unit": "TFLOP/s", "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS},
+                    "status": rc})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -184,6 +273,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "2d":
+        if rank == 0:
+            run_aux(args)
         return
 
     import numpy as np
@@ -254,7 +347,8 @@ def main():
     nnode = N ** DIM
     nz = fma / 2.0
     bfly = DIM * (1 << DIM) * (M + 1) ** DIM
-    flops = {"p_half": nnode * (2 * nz + DIM * bfly), "u_half": nnode * (2 * nz + bfly)}
+    nq = (M + 1) ** DIM
+    flops = {"p_half": nnode * (2 * nz + DIM * bfly + nq), "u_half": nnode * (2 * nz + bfly + DIM * nq)}
     dom = max(("p_half", "u_half"), key=lambda k: ktimes[k])
     mean_s = ktimes[dom] / kcount[dom] / 1e3
     achieved = flops[dom] / mean_s

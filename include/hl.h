@@ -71,9 +71,17 @@ enum {
     HL_ESTATE = -6       /* call not valid in the handle's state               */
 };
 
-/* Arithmetic modes for hl_set_precision. */
+/* Arithmetic modes for hl_set_precision.  The node data are binary64 and
+ * every increment is added to them in binary64 in all modes. */
 enum {
-    HL_FP64 = 0          /* every operation in IEEE binary64                   */
+    HL_FP64 = 0,         /* every operation in IEEE binary64                   */
+    HL_FP32 = 1,         /* interpolation + evolution contraction on the FP32
+                            pipe: data and operator rounded to binary32, FP32
+                            accumulation                                     */
+    HL_FP32_COMP = 2     /* as HL_FP32 plus a split-precision correction: data
+                            and operator split into binary32 hi + lo parts,
+                            hi*hi accumulated apart from hi*lo + lo*hi, the two
+                            sums added in binary64                           */
 };
 
 /*
@@ -91,6 +99,21 @@ enum {
  * HL_ECUDA if device set-up fails.  The state is zero after creation.
  */
 int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out);
+
+/*
+ * hl_create_batch -- one handle for n_shots independent grids of the same
+ * dim and m, stepped together (every launch covers all shots; hl_step is
+ * captured as one CUDA graph by default).
+ *   n_shots : 1..256; batched handles allow m <= 3.
+ *   n_cells : n_shots*dim entries, shot-major.
+ *   dt      : n_shots time steps (each below that shot's min h).
+ * Host layout of a batch: the single-grid layouts of the shots concatenated
+ * in shot order (p blocks, then separately u blocks); the device layout is
+ * the concatenation of each shot's slot-major blocks.  hl_get_fields reports
+ * the times of shot 0; shot s is at steps*dt[s] (see hl_info).
+ * Validation and error codes as hl_create.
+ */
+int hl_create_batch(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out);
 
 /*
  * hl_set_initial -- copy host initial data (host layout) to the device.
@@ -173,7 +196,26 @@ int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev);
 int hl_set_source(hl_solver *h, const double *x0, double sigma, double f0, double amp);
 
 /*
- * hl_set_precision -- select the arithmetic mode (HL_FP64 only for now).
+ * hl_set_sources -- per-shot point sources for a batched handle (arrays of
+ * n_shots entries; x0 has n_shots*dim).  Shots with amp[s] = 0 get none.
+ * Same source model and injection as hl_set_source.
+ */
+int hl_set_sources(hl_solver *h, const double *x0, const double *sigma, const double *f0, const double *amp);
+
+/*
+ * hl_autotune -- time every tile shape (HL_OPT_TILE) on scratch copies of the
+ * state (the solution is not advanced), steps_per_trial steps each after one
+ * warm-up step, and keep the fastest.  best_tile receives its index and
+ * ms_per_tile[HL_NUM_TILES] (may be NULL) the milliseconds per step of each
+ * shape (-1 for shapes not tried).  Allocates scratch equal to the state size.
+ */
+int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile, double *ms_per_tile);
+
+/*
+ * hl_set_precision -- select the arithmetic mode (HL_FP64, HL_FP32,
+ * HL_FP32_COMP).  The FP32 modes need m <= 3 (m <= 2 in 3D) and, on a batch, the same
+ * dt/h on every shot; they return HL_EINVAL otherwise.  Takes effect at the
+ * next hl_step.
  */
 int hl_set_precision(hl_solver *h, int mode);
 
@@ -182,10 +224,19 @@ enum {
     HL_OPT_KERNEL_PATH = 1,  /* 0 = automatic; 1 = one persistent CTA with the
                                 whole state in shared memory (tiny grids only);
                                 2 = one grid launch per half-step             */
-    HL_OPT_TIMING = 2        /* 1 = bracket every kernel launch with CUDA events
+    HL_OPT_TIMING = 2,       /* 1 = bracket every kernel launch with CUDA events
                                 on the handle's stream (read by hl_kernel_times);
-                                0 = off (default)                             */
+                                0 = off (default).  Not recorded in graph mode. */
+    HL_OPT_GRAPH = 3,        /* 1 = capture each hl_step call (all its launches)
+                                as one CUDA graph and launch that; default 1 for
+                                batched handles, 0 otherwise                  */
+    HL_OPT_TILE = 4          /* thread-block tile shape index 0..HL_NUM_TILES-1
+                                (nodes per block along x and y: 128x1, 256x1,
+                                64x2, 32x4, 32x8, 64x4, 16x8, 16x16; dim = 1
+                                folds the tile into x); hl_autotune picks one  */
 };
+
+#define HL_NUM_TILES 8
 
 /*
  * hl_set_option -- set an execution option (see the HL_OPT_* values).
@@ -205,6 +256,17 @@ int hl_set_option(hl_solver *h, int option, int64_t value);
 int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches);
 
 /*
+ * hl_operator_table -- the fused per-node operator the FP64 kernels apply,
+ * for inspection (host only, no CUDA call).  out receives dim*nq*nq doubles,
+ * entry (i, l, s) at (i*nq + l)*nq + s: the increment of output slot s per
+ * unit of the vertex butterfly of input slot l, direction i, with
+ * lam[k] = dt/(2 h_k).  It is W_i (H x ... x H) restricted to the all-lower
+ * vertex block and negated (Section 2, eqs. interp and final1; Section 3.1.2,
+ * eqs. pdup and vdup), composed in double-double and rounded once.
+ */
+int hl_operator_table(int dim, int m, const double *lam, double *out);
+
+/*
  * hl_op_counts -- floating-point work of the FP64 kernels per node and full
  * step for (dim, m): multiply-adds (one multiply-add = 2 flops) and plain
  * additions of the vertex butterflies.  Used for roofline accounting.
@@ -212,8 +274,8 @@ int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches);
 int hl_op_counts(int dim, int m, double *fma_per_node_step, double *add_per_node_step);
 
 /*
- * hl_info -- sizes of a handle: nnode (nodes per grid), nq ((m+1)^dim) and
- * the number of completed steps.  Any pointer may be NULL.
+ * hl_info -- sizes of a handle: nnode (nodes per grid, summed over the shots
+ * of a batch), nq ((m+1)^dim) and the number of completed steps.  Any pointer may be NULL.
  */
 int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
 

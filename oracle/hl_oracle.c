@@ -47,14 +47,31 @@
 #include <omp.h>
 #endif
 
+/* The source is precision-generic.  The default build uses IEEE binary64
+ * (the paper's precision, Section 6).  Built with -DORC_LONG it uses long
+ * double (x87 80-bit on x86-64, binary128 on aarch64): the same steps with a
+ * smaller rounding error, used to judge long runs against a 1e-12 bar that
+ * lies below the binary64 build's own accumulated rounding. */
+#ifdef ORC_LONG
+typedef long double orc_real;
+#define ORC_POW powl
+#define ORC_EXP expl
+#define ORC_FLOOR floorl
+#else
+typedef double orc_real;
+#define ORC_POW pow
+#define ORC_EXP exp
+#define ORC_FLOOR floor
+#endif
+
 #define ORC_MAXD 3
 #define ORC_MAXM 6
 #define ORC_MAXA (2 * ORC_MAXM + 2)
 
-static double orc_fact(int n)
+static orc_real orc_fact(int n)
 {
-    double f = 1.0;
-    for (int k = 2; k <= n; ++k) f *= (double)k;
+    orc_real f = 1.0;
+    for (int k = 2; k <= n; ++k) f *= (orc_real)k;
     return f;
 }
 
@@ -70,13 +87,13 @@ static int64_t ipow(int64_t b, int e)
  * stacked data index r = bit*(m+1) + q matches the paper's [v^L; v^R].
  * coef[a], a = a_0 + A*(a_1 + A*a_2), A = 2m+2, receives the scaled Taylor
  * coefficients of the interpolant at the cell centre. */
-static void orc_reconstruct(int d, int m, const double *H, const double *vtx, double *coef)
+static void orc_reconstruct(int d, int m, const orc_real *H, const orc_real *vtx, orc_real *coef)
 {
     const int n = m + 1, A = 2 * m + 2;
     const int64_t nq = ipow(n, d);
     const int64_t tot = ipow(A, d);
-    double *x = (double *)malloc(sizeof(double) * (size_t)tot);
-    double *y = (double *)malloc(sizeof(double) * (size_t)tot);
+    orc_real *x = (orc_real *)malloc(sizeof(orc_real) * (size_t)tot);
+    orc_real *y = (orc_real *)malloc(sizeof(orc_real) * (size_t)tot);
     /* scatter vertex data into the stacked tensor x[r_0 + A*(r_1 + A*r_2)] */
     for (int v = 0; v < (1 << d); ++v) {
         for (int64_t q = 0; q < nq; ++q) {
@@ -97,13 +114,13 @@ static void orc_reconstruct(int d, int m, const double *H, const double *vtx, do
         for (int64_t idx = 0; idx < tot; ++idx) {
             int ak = (int)((idx / sk) % A);
             int64_t base = idx - (int64_t)ak * sk;
-            double acc = 0.0;
+            orc_real acc = 0.0;
             for (int r = 0; r < A; ++r) acc += H[ak * A + r] * x[base + (int64_t)r * sk];
             y[idx] = acc;
         }
-        memcpy(x, y, sizeof(double) * (size_t)tot);
+        memcpy(x, y, sizeof(orc_real) * (size_t)tot);
     }
-    memcpy(coef, x, sizeof(double) * (size_t)tot);
+    memcpy(coef, x, sizeof(orc_real) * (size_t)tot);
     free(x);
     free(y);
 }
@@ -115,11 +132,11 @@ static void orc_reconstruct(int d, int m, const double *H, const double *vtx, do
  *                          * lam_l^(2 beta_l + [l==i]) * coef[s + 2 beta + e_i]
  * where lam_l = dt/(2 h_l).  Returns the (positive) series value; the caller
  * subtracts it (v = -u sign convention). */
-static double orc_series(int d, int m, const double *lam, const double *coef, const int *s, int i)
+static orc_real orc_series(int d, int m, const orc_real *lam, const orc_real *coef, const int *s, int i)
 {
     const int A = 2 * m + 2;
     const int kmax = d * (2 * m + 1); /* generous bound; out-of-range terms are skipped */
-    double total = 0.0;
+    orc_real total = 0.0;
     for (int k = 0; k <= kmax; ++k) {
         /* enumerate beta with |beta| = k, beta_l in 0..k */
         int beta[ORC_MAXD] = {0, 0, 0};
@@ -133,13 +150,13 @@ static double orc_series(int d, int m, const double *lam, const double *coef, co
                 beta[2] = b2;
                 int ok = 1;
                 int64_t aidx = 0, stride = 1;
-                double c = 2.0 / orc_fact(2 * k + 1) * orc_fact(k);
+                orc_real c = 2.0 / orc_fact(2 * k + 1) * orc_fact(k);
                 for (int l = 0; l < d; ++l) {
                     int a = s[l] + 2 * beta[l] + (l == i ? 1 : 0);
                     if (a > 2 * m + 1) { ok = 0; break; }
                     c *= 1.0 / orc_fact(beta[l]);
                     c *= orc_fact(a) / orc_fact(s[l]);
-                    c *= pow(lam[l], (double)(a - s[l]));
+                    c *= ORC_POW(lam[l], (orc_real)(a - s[l]));
                     aidx += (int64_t)a * stride;
                     stride *= A;
                 }
@@ -155,14 +172,14 @@ static double orc_series(int d, int m, const double *lam, const double *coef, co
  * dst one pressure block; mode 1 (u-half): src holds pressure, dst d velocity
  * blocks.  vtx[(comp*2^d + v)*nq + q]; incr[comp*nq + q] receives the
  * increment to ADD to the target's own data. */
-void oracle_node_update(int d, int m, const double *lam, const double *H, int mode,
-                        const double *vtx, double *incr)
+void oracle_node_update(int d, int m, const orc_real *lam, const orc_real *H, int mode,
+                        const orc_real *vtx, orc_real *incr)
 {
     const int n = m + 1, A = 2 * m + 2;
     const int64_t nq = ipow(n, d);
     const int64_t nv = (int64_t)1 << d;
     const int ncs = mode == 0 ? d : 1;
-    double *coef = (double *)malloc(sizeof(double) * (size_t)(ncs * ipow(A, d)));
+    orc_real *coef = (orc_real *)malloc(sizeof(orc_real) * (size_t)(ncs * ipow(A, d)));
     for (int c = 0; c < ncs; ++c)
         orc_reconstruct(d, m, H, vtx + (int64_t)c * nv * nq, coef + (int64_t)c * ipow(A, d));
     for (int64_t q = 0; q < nq; ++q) {
@@ -170,7 +187,7 @@ void oracle_node_update(int d, int m, const double *lam, const double *H, int mo
         int64_t qq = q;
         for (int k = 0; k < d; ++k) { s[k] = (int)(qq % n); qq /= n; }
         if (mode == 0) {
-            double acc = 0.0;
+            orc_real acc = 0.0;
             for (int i = 0; i < d; ++i) acc += orc_series(d, m, lam, coef + (int64_t)i * ipow(A, d), s, i);
             incr[q] = -acc;
         } else {
@@ -184,8 +201,8 @@ void oracle_node_update(int d, int m, const double *lam, const double *H, int mo
  * takes dual nodes j-1 and j as the ends of its cell on each axis; mode 1:
  * u-half, the dual node j takes primal nodes j and j+1.  src is read only,
  * dst is updated in place (each target reads only its own dst data). */
-void oracle_half_step(int d, int m, const int64_t *ncell, const double *lam, const double *H,
-                      int mode, const double *src, double *dst)
+void oracle_half_step(int d, int m, const int64_t *ncell, const orc_real *lam, const orc_real *H,
+                      int mode, const orc_real *src, orc_real *dst)
 {
     const int n = m + 1;
     const int64_t nq = ipow(n, d);
@@ -202,8 +219,8 @@ void oracle_half_step(int d, int m, const int64_t *ncell, const double *lam, con
         int64_t j[ORC_MAXD] = {0, 0, 0};
         int64_t t = node;
         for (int k = 0; k < d; ++k) { j[k] = t % N[k]; t /= N[k]; }
-        double *vtx = (double *)malloc(sizeof(double) * (size_t)(ncs * nv * nq));
-        double *inc = (double *)malloc(sizeof(double) * (size_t)(ncd * nq));
+        orc_real *vtx = (orc_real *)malloc(sizeof(orc_real) * (size_t)(ncs * nv * nq));
+        orc_real *inc = (orc_real *)malloc(sizeof(orc_real) * (size_t)(ncd * nq));
         /* step 1: gather */
         for (int64_t v = 0; v < nv; ++v) {
             int64_t vn = 0, stride = 1;
@@ -232,9 +249,9 @@ void oracle_half_step(int d, int m, const int64_t *ncell, const double *lam, con
  * out[(c*n_sample + k)*nq + q] = dst[c][nodes[k]][q] + increment, with the
  * same gather and node update.  dst is read only.  Used to check a large run
  * at sampled nodes from its own state one half-step earlier. */
-void oracle_half_step_nodes(int d, int m, const int64_t *ncell, const double *lam, const double *H,
-                            int mode, const double *src, const double *dst, const int64_t *nodes,
-                            int64_t n_sample, double *out)
+void oracle_half_step_nodes(int d, int m, const int64_t *ncell, const orc_real *lam, const orc_real *H,
+                            int mode, const orc_real *src, const orc_real *dst, const int64_t *nodes,
+                            int64_t n_sample, orc_real *out)
 {
     const int n = m + 1;
     const int64_t nq = ipow(n, d);
@@ -252,8 +269,8 @@ void oracle_half_step_nodes(int d, int m, const int64_t *ncell, const double *la
         int64_t j[ORC_MAXD] = {0, 0, 0};
         int64_t t = node;
         for (int k = 0; k < d; ++k) { j[k] = t % N[k]; t /= N[k]; }
-        double *vtx = (double *)malloc(sizeof(double) * (size_t)(ncs * nv * nq));
-        double *inc = (double *)malloc(sizeof(double) * (size_t)(ncd * nq));
+        orc_real *vtx = (orc_real *)malloc(sizeof(orc_real) * (size_t)(ncs * nv * nq));
+        orc_real *inc = (orc_real *)malloc(sizeof(orc_real) * (size_t)(ncd * nq));
         for (int64_t v = 0; v < nv; ++v) {
             int64_t vn = 0, stride = 1;
             for (int k = 0; k < d; ++k) {
@@ -277,8 +294,8 @@ void oracle_half_step_nodes(int d, int m, const int64_t *ncell, const double *la
 }
 
 /* n_steps full steps: p-half then u-half (p at t -> t+dt, u at t+dt/2 -> t+3dt/2). */
-void oracle_run(int d, int m, const int64_t *ncell, const double *lam, const double *H,
-                double *p, double *u, int64_t n_steps)
+void oracle_run(int d, int m, const int64_t *ncell, const orc_real *lam, const orc_real *H,
+                orc_real *p, orc_real *u, int64_t n_steps)
 {
     for (int64_t s = 0; s < n_steps; ++s) {
         oracle_half_step(d, m, ncell, lam, H, 0, u, p);
@@ -291,60 +308,60 @@ void oracle_run(int d, int m, const int64_t *ncell, const double *lam, const dou
  * forced experiments add a source z(x,t) to the pressure equation (Section 4,
  * eq. waveEq1D) without stating its time discretisation; here the source
  *     f(x,t) = amp * R(t) * g(x),
- *     R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),  t0 = 1.2/f0,
- *     g(x) = exp(-|x - x0|^2 / (2 sigma^2))   (nearest periodic image),
+ *     R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) ORC_EXP(-pi^2 f0^2 (t-t0)^2),  t0 = 1.2/f0,
+ *     g(x) = ORC_EXP(-|x - x0|^2 / (2 sigma^2))   (nearest periodic image),
  * enters the p-half by the midpoint rule: p~_a += dt * amp * R(t_n + dt/2) * g~_a,
  * with g~_a the exact scaled derivatives prod_k h_k^{a_k}/a_k! d^{a_k} g_k. */
-static double orc_ricker(double t, double f0)
+static orc_real orc_ricker(orc_real t, orc_real f0)
 {
-    const double pi = 3.14159265358979323846;
-    const double t0 = 1.2 / f0;
-    const double arg = pi * pi * f0 * f0 * (t - t0) * (t - t0);
-    return (1.0 - 2.0 * arg) * exp(-arg);
+    const orc_real pi = 3.14159265358979323846;
+    const orc_real t0 = 1.2 / f0;
+    const orc_real arg = pi * pi * f0 * f0 * (t - t0) * (t - t0);
+    return (1.0 - 2.0 * arg) * ORC_EXP(-arg);
 }
 
-/* scaled derivatives (h^a/a!) d^a/dx^a exp(-z^2/2), z = (x - c)/sigma, a = 0..m:
- * d^a exp(-z^2/2)/dx^a = (-1/sigma)^a He_a(z) exp(-z^2/2) (probabilists' Hermite). */
-static void orc_gauss_1d(double dx, double sigma, double h, int m, double *out)
+/* scaled derivatives (h^a/a!) d^a/dx^a ORC_EXP(-z^2/2), z = (x - c)/sigma, a = 0..m:
+ * d^a ORC_EXP(-z^2/2)/dx^a = (-1/sigma)^a He_a(z) ORC_EXP(-z^2/2) (probabilists' Hermite). */
+static void orc_gauss_1d(orc_real dx, orc_real sigma, orc_real h, int m, orc_real *out)
 {
-    const double z = dx / sigma;
-    const double g = exp(-0.5 * z * z);
-    double he_prev = 1.0, he = z;
+    const orc_real z = dx / sigma;
+    const orc_real g = ORC_EXP(-0.5 * z * z);
+    orc_real he_prev = 1.0, he = z;
     for (int a = 0; a <= m; ++a) {
-        double hea = a == 0 ? 1.0 : (a == 1 ? z : 0.0);
+        orc_real hea = a == 0 ? 1.0 : (a == 1 ? z : 0.0);
         if (a >= 2) {
-            double next = z * he - (double)(a - 1) * he_prev;
+            orc_real next = z * he - (orc_real)(a - 1) * he_prev;
             he_prev = he;
             he = next;
             hea = he;
         }
-        out[a] = pow(-h / sigma, (double)a) / orc_fact(a) * hea * g;
+        out[a] = ORC_POW(-h / sigma, (orc_real)a) / orc_fact(a) * hea * g;
     }
 }
 
-void oracle_add_source(int d, int m, const int64_t *ncell, const double *x0, double sigma, double f0,
-                       double amp, double t_mid, double dt, double *p)
+void oracle_add_source(int d, int m, const int64_t *ncell, const orc_real *x0, orc_real sigma, orc_real f0,
+                       orc_real amp, orc_real t_mid, orc_real dt, orc_real *p)
 {
     const int n = m + 1;
     const int64_t nq = ipow(n, d);
     int64_t N[ORC_MAXD] = {1, 1, 1};
     int64_t nnode = 1;
     for (int k = 0; k < d; ++k) { N[k] = ncell[k]; nnode *= N[k]; }
-    const double w = dt * amp * orc_ricker(t_mid, f0);
+    const orc_real w = dt * amp * orc_ricker(t_mid, f0);
 #pragma omp parallel for schedule(static)
     for (int64_t node = 0; node < nnode; ++node) {
-        double fac[ORC_MAXD][ORC_MAXM + 1];
+        orc_real fac[ORC_MAXD][ORC_MAXM + 1];
         int64_t t = node;
         for (int k = 0; k < d; ++k) {
             const int64_t j = t % N[k];
             t /= N[k];
-            const double h = 1.0 / (double)N[k];
-            double dx = (double)j * h - x0[k];
-            dx -= floor(dx + 0.5);          /* nearest periodic image */
+            const orc_real h = 1.0 / (orc_real)N[k];
+            orc_real dx = (orc_real)j * h - x0[k];
+            dx -= ORC_FLOOR(dx + 0.5);          /* nearest periodic image */
             orc_gauss_1d(dx, sigma, h, m, fac[k]);
         }
         for (int64_t q = 0; q < nq; ++q) {
-            double g = 1.0;
+            orc_real g = 1.0;
             int64_t qq = q;
             for (int k = 0; k < d; ++k) { g *= fac[k][qq % n]; qq /= n; }
             p[node * nq + q] += w * g;
@@ -353,13 +370,13 @@ void oracle_add_source(int d, int m, const int64_t *ncell, const double *x0, dou
 }
 
 /* n_steps steps with the point source added after each p-half. */
-void oracle_run_source(int d, int m, const int64_t *ncell, const double *lam, const double *H, double dt,
-                       const double *x0, double sigma, double f0, double amp, int64_t step0,
-                       double *p, double *u, int64_t n_steps)
+void oracle_run_source(int d, int m, const int64_t *ncell, const orc_real *lam, const orc_real *H, orc_real dt,
+                       const orc_real *x0, orc_real sigma, orc_real f0, orc_real amp, int64_t step0,
+                       orc_real *p, orc_real *u, int64_t n_steps)
 {
     for (int64_t s = 0; s < n_steps; ++s) {
         oracle_half_step(d, m, ncell, lam, H, 0, u, p);
-        oracle_add_source(d, m, ncell, x0, sigma, f0, amp, ((double)(step0 + s) + 0.5) * dt, dt, p);
+        oracle_add_source(d, m, ncell, x0, sigma, f0, amp, ((orc_real)(step0 + s) + 0.5) * dt, dt, p);
         oracle_half_step(d, m, ncell, lam, H, 1, p, u);
     }
 }

@@ -13,20 +13,48 @@
 
 using namespace hl;
 
-struct hl_solver {
-    int dim = 0, m = 0;
+namespace {
+
+// tile (thread block) shapes the autotuner chooses from: (TX, TY)
+constexpr int kTiles[][2] = {{128, 1}, {256, 1}, {64, 2}, {32, 4}, {32, 8}, {64, 4}, {16, 8}, {16, 16}};
+constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+static_assert(kNumTiles == HL_NUM_TILES, "tile table and header disagree");
+
+struct Shot {
     int64_t n[3] = {1, 1, 1};
     double dt = 0.0;
     double lam[3] = {0.0, 0.0, 0.0};
-    int64_t nnode = 0, nq = 0;
+    int64_t nnode = 0;
+    int64_t p_off = 0;   // element offset in the slot-major p array (and host p array)
+    int64_t u_off = 0;   // element offset in the slot-major u array (and host u array)
+};
+
+}  // namespace
+
+struct hl_solver {
+    int dim = 0, m = 0;
+    int64_t nq = 0;
+    std::vector<Shot> shots;
+    int64_t p_elems = 0, u_elems = 0;           // totals over shots
     double *p = nullptr, *u = nullptr;          // active device state, slot-major
     double *p_own = nullptr, *u_own = nullptr;  // library-owned state
-    double *staging = nullptr;                  // host-layout staging, (dim+1)*nnode*nq
+    double *staging = nullptr;                  // host-layout staging, p_elems + u_elems
     unsigned *status = nullptr;                 // device status word
     unsigned *status_host = nullptr;            // pinned mirror
+    std::vector<double> coef;                   // n_shots dense tables (shot 0 first)
     double *coef_dev = nullptr;
-    std::vector<double> coef;
+    bool per_shot_coef = false;
+    // tiles
+    int tile = 0;
+    std::vector<ShotDesc> shot_desc;
+    ShotDesc *shot_desc_dev = nullptr;
+    int total_tiles = 0;
+    // streams and graph capture
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graph = false;
     int64_t steps = 0;
     bool poisoned = false;
     int precision = HL_FP64;
@@ -35,14 +63,18 @@ struct hl_solver {
     // opt-in kernel timing (HL_OPT_TIMING)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    struct Pending { size_t first; int64_t nsteps; bool small; };
+    struct Pending {
+        size_t first;
+        int64_t nsteps;
+        bool small;
+    };
     std::vector<Pending> pending;
     size_t ev_used = 0;
     double t_p_ms = 0.0, t_u_ms = 0.0, t_small_ms = 0.0;
     int64_t n_p = 0, n_u = 0, n_small = 0;
-    // point source
+    // point sources
     SourceDesc src;
-    int *src_nodes = nullptr;
+    int *src_node = nullptr, *src_shot = nullptr;
     double *src_table = nullptr;
 };
 
@@ -63,10 +95,10 @@ static int fail_cuda(hl_solver *h, cudaError_t e, const char *what)
     return set_err(h, HL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define HL_CK(h, call)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return fail_cuda(h, e_, #call); \
+#define HL_CK(h, call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return fail_cuda(h, e_, #call);  \
     } while (0)
 
 static int resolve_timing(hl_solver *h);
@@ -78,61 +110,127 @@ static int check_usable(hl_solver *h)
     return HL_OK;
 }
 
+static void free_source(hl_solver *h)
+{
+    if (h->src_node) cudaFree(h->src_node);
+    if (h->src_shot) cudaFree(h->src_shot);
+    if (h->src_table) cudaFree(h->src_table);
+    h->src_node = h->src_shot = nullptr;
+    h->src_table = nullptr;
+    h->src = SourceDesc();
+}
+
 static void release(hl_solver *h)
 {
     if (!h) return;
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    if (h->src_nodes) cudaFree(h->src_nodes);
-    if (h->src_table) cudaFree(h->src_table);
+    free_source(h);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->p_own) cudaFree(h->p_own);
     if (h->u_own) cudaFree(h->u_own);
     if (h->staging) cudaFree(h->staging);
     if (h->status) cudaFree(h->status);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->coef_dev) cudaFree(h->coef_dev);
+    if (h->shot_desc_dev) cudaFree(h->shot_desc_dev);
     delete h;
 }
 
-extern "C" int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out)
+// (re)build the device shot table for tile shape `tile`
+static int build_tiles(hl_solver *h, int tile)
+{
+    int tx = kTiles[tile][0], ty = kTiles[tile][1];
+    if (h->dim == 1) {  // one row of nodes: fold the tile into x
+        tx *= ty;
+        ty = 1;
+    }
+    std::vector<ShotDesc> sd(h->shots.size());
+    int64_t tiles = 0;
+    for (size_t s = 0; s < h->shots.size(); ++s) {
+        const Shot &sh = h->shots[s];
+        ShotDesc &d = sd[s];
+        for (int k = 0; k < 3; ++k) d.n[k] = (int)sh.n[k];
+        d.tiles[0] = (int)((sh.n[0] + tx - 1) / tx);
+        d.tiles[1] = (int)((sh.n[1] + ty - 1) / ty);
+        d.tiles[2] = (int)sh.n[2];
+        d.nnode = sh.nnode;
+        d.p_off = sh.p_off;
+        d.u_off = sh.u_off;
+        d.tile_begin = (int)tiles;
+        d.pad = 0;
+        tiles += (int64_t)d.tiles[0] * d.tiles[1] * d.tiles[2];
+        if (tiles >= (int64_t(1) << 31)) return set_err(h, HL_EINVAL, "too many tiles for one launch");
+    }
+    if (!h->shot_desc_dev) HL_CK(h, cudaMalloc(&h->shot_desc_dev, sd.size() * sizeof(ShotDesc)));
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    HL_CK(h, cudaMemcpy(h->shot_desc_dev, sd.data(), sd.size() * sizeof(ShotDesc), cudaMemcpyHostToDevice));
+    h->shot_desc = sd;
+    h->total_tiles = (int)tiles;
+    h->tile = tile;
+    return HL_OK;
+}
+
+static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out)
 {
     if (out) *out = nullptr;
     if (!out) return set_err(nullptr, HL_EINVAL, "out is NULL");
     if (dim < 1 || dim > 3) return set_err(nullptr, HL_EINVAL, "dim must be 1, 2 or 3");
     if (m < 0 || m > 6) return set_err(nullptr, HL_EINVAL, "m must be in 0..6");
     if (dim == 3 && m > 3) return set_err(nullptr, HL_EINVAL, "dim = 3 supports m <= 3");
-    if (!n_cells) return set_err(nullptr, HL_EINVAL, "n_cells is NULL");
-    int64_t nnode = 1;
-    double hmin = 1.0;
-    for (int k = 0; k < dim; ++k) {
-        if (n_cells[k] < 2) return set_err(nullptr, HL_EINVAL, "every n_cells entry must be >= 2");
-        if (n_cells[k] > (int64_t(1) << 30)) return set_err(nullptr, HL_EINVAL, "n_cells entry too large");
-        nnode *= n_cells[k];
-        if (nnode >= (int64_t(1) << 31)) return set_err(nullptr, HL_EINVAL, "more than 2^31-1 nodes per grid");
-        hmin = std::fmin(hmin, 1.0 / (double)n_cells[k]);
+    if (n_shots < 1 || n_shots > kMaxShots) return set_err(nullptr, HL_EINVAL, "n_shots must be in 1..256");
+    if (n_shots > 1 && m > 3) return set_err(nullptr, HL_EINVAL, "batched handles support m <= 3");
+    if (!n_cells || !dt) return set_err(nullptr, HL_EINVAL, "n_cells or dt is NULL");
+    std::vector<Shot> shots(n_shots);
+    int64_t nq = 1;
+    for (int k = 0; k < dim; ++k) nq *= (m + 1);
+    int64_t p_elems = 0;
+    for (int s = 0; s < n_shots; ++s) {
+        Shot &sh = shots[s];
+        double hmin = 1.0;
+        sh.nnode = 1;
+        for (int k = 0; k < dim; ++k) {
+            const int64_t nk = n_cells[(size_t)s * dim + k];
+            if (nk < 2) return set_err(nullptr, HL_EINVAL, "every n_cells entry must be >= 2");
+            if (nk > (int64_t(1) << 30)) return set_err(nullptr, HL_EINVAL, "n_cells entry too large");
+            sh.n[k] = nk;
+            sh.nnode *= nk;
+            if (sh.nnode >= (int64_t(1) << 31)) return set_err(nullptr, HL_EINVAL, "more than 2^31-1 nodes per grid");
+            hmin = std::fmin(hmin, 1.0 / (double)nk);
+        }
+        if (!(dt[s] > 0.0) || !std::isfinite(dt[s])) return set_err(nullptr, HL_EINVAL, "dt must be finite and > 0");
+        if (!(dt[s] < hmin)) return set_err(nullptr, HL_EINVAL, "dt must be below min h (c dt/dx < 1)");
+        sh.dt = dt[s];
+        for (int k = 0; k < dim; ++k) sh.lam[k] = dt[s] * (double)sh.n[k] / 2.0;
+        sh.p_off = p_elems;
+        sh.u_off = p_elems * dim;
+        p_elems += sh.nnode * nq;
+        if (p_elems * (dim + 1) > (int64_t(1) << 38)) return set_err(nullptr, HL_EINVAL, "state too large");
     }
-    if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(nullptr, HL_EINVAL, "dt must be finite and > 0");
-    if (!(dt < hmin)) return set_err(nullptr, HL_EINVAL, "dt must be below min h (c dt/dx < 1)");
 
     hl_solver *h = new hl_solver();
     h->dim = dim;
     h->m = m;
-    h->dt = dt;
-    h->nnode = nnode;
-    h->nq = 1;
-    for (int k = 0; k < dim; ++k) {
-        h->n[k] = n_cells[k];
-        h->lam[k] = dt * (double)n_cells[k] / 2.0;
-        h->nq *= (m + 1);
+    h->nq = nq;
+    h->shots = shots;
+    h->p_elems = p_elems;
+    h->u_elems = p_elems * dim;
+    h->per_shot_coef = n_shots > 1;
+    h->use_graph = n_shots > 1;
+    for (int s = 0; s < n_shots; ++s) {
+        std::vector<double> c;
+        if (!build_operator(dim, m, shots[s].lam, c)) {
+            delete h;
+            return set_err(nullptr, HL_EINVAL, "operator construction failed its structural check");
+        }
+        h->coef.insert(h->coef.end(), c.begin(), c.end());
     }
-    if (!build_operator(dim, m, h->lam, h->coef)) {
-        delete h;
-        return set_err(nullptr, HL_EINVAL, "operator construction failed its structural check");
-    }
-    const size_t pbytes = (size_t)nnode * h->nq * sizeof(double);
+    const size_t pb = (size_t)p_elems * sizeof(double);
     cudaError_t e;
-    if ((e = cudaMalloc(&h->p_own, pbytes)) != cudaSuccess ||
-        (e = cudaMalloc(&h->u_own, pbytes * dim)) != cudaSuccess ||
-        (e = cudaMalloc(&h->staging, pbytes * (dim + 1))) != cudaSuccess ||
+    if ((e = cudaMalloc(&h->p_own, pb)) != cudaSuccess || (e = cudaMalloc(&h->u_own, pb * dim)) != cudaSuccess ||
+        (e = cudaMalloc(&h->staging, pb * (dim + 1))) != cudaSuccess ||
         (e = cudaMalloc(&h->status, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMallocHost(&h->status_host, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&h->coef_dev, h->coef.size() * sizeof(double))) != cudaSuccess) {
@@ -142,25 +240,46 @@ extern "C" int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_s
         release(h);
         return set_err(nullptr, code, msg);
     }
-    if ((e = cudaMemset(h->p_own, 0, pbytes)) != cudaSuccess || (e = cudaMemset(h->u_own, 0, pbytes * dim)) != cudaSuccess ||
+    if ((e = cudaMemset(h->p_own, 0, pb)) != cudaSuccess || (e = cudaMemset(h->u_own, 0, pb * dim)) != cudaSuccess ||
         (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemcpy(h->coef_dev, h->coef.data(), h->coef.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
         std::string msg = std::string("device set-up failed: ") + cudaGetErrorString(e);
         release(h);
         return set_err(nullptr, HL_ECUDA, msg);
     }
     h->p = h->p_own;
     h->u = h->u_own;
+    if (build_tiles(h, 0) != HL_OK) {
+        std::string msg = h->err;
+        release(h);
+        return set_err(nullptr, HL_ECUDA, msg);
+    }
     *out = h;
     return HL_OK;
+}
+
+extern "C" int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out)
+{
+    return create_common(dim, m, 1, n_cells, &dt, out);
+}
+
+extern "C" int hl_create_batch(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out)
+{
+    return create_common(dim, m, n_shots, n_cells, dt, out);
 }
 
 extern "C" void hl_destroy(hl_solver *h)
 {
     if (!h) return;
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    else cudaDeviceSynchronize();
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    else
+        cudaDeviceSynchronize();
+    if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
     release(h);
 }
 
@@ -183,7 +302,18 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (mode != HL_FP64) return set_err(h, HL_EINVAL, "unknown precision mode");
+    if (mode != HL_FP64 && mode != HL_FP32 && mode != HL_FP32_COMP)
+        return set_err(h, HL_EINVAL, "unknown precision mode");
+    if (mode != HL_FP64) {
+        if (h->m > 3 || (h->dim == 3 && h->m > 2))
+            return set_err(h, HL_EINVAL, "mixed precision supports m <= 3 (m <= 2 in 3D)");
+        // one FP32 table serves every shot: the shots' lam must agree (they do
+        // when every dt is C_CFL times that shot's h)
+        for (const Shot &s : h->shots)
+            for (int k = 0; k < h->dim; ++k)
+                if (std::fabs(s.lam[k] - h->shots[0].lam[k]) > 1e-12 * std::fabs(h->shots[0].lam[k]))
+                    return set_err(h, HL_EINVAL, "mixed precision needs the same dt/h on every shot");
+    }
     h->precision = mode;
     return HL_OK;
 }
@@ -192,56 +322,43 @@ extern "C" int hl_set_option(hl_solver *h, int option, int64_t value)
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (option == HL_OPT_KERNEL_PATH) {
+    switch (option) {
+    case HL_OPT_KERNEL_PATH:
         if (value < 0 || value > 2) return set_err(h, HL_EINVAL, "kernel path must be 0, 1 or 2");
         h->path = (int)value;
         return HL_OK;
-    }
-    if (option == HL_OPT_TIMING) {
+    case HL_OPT_TIMING:
         if (value < 0 || value > 1) return set_err(h, HL_EINVAL, "timing must be 0 or 1");
         HL_CK(h, cudaStreamSynchronize(h->stream));
         if (h->timing) {
-            int rc2 = resolve_timing(h);
-            if (rc2) return rc2;
+            rc = resolve_timing(h);
+            if (rc) return rc;
         }
         h->timing = value != 0;
         return HL_OK;
+    case HL_OPT_GRAPH:
+        if (value < 0 || value > 1) return set_err(h, HL_EINVAL, "graph must be 0 or 1");
+        h->use_graph = value != 0;
+        return HL_OK;
+    case HL_OPT_TILE:
+        if (value < 0 || value >= kNumTiles) return set_err(h, HL_EINVAL, "tile index out of range");
+        return build_tiles(h, (int)value);
+    default:
+        return set_err(h, HL_EINVAL, "unknown option");
     }
-    return set_err(h, HL_EINVAL, "unknown option");
 }
 
-extern "C" int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches)
-{
-    int rc = check_usable(h);
-    if (rc) return rc;
-    HL_CK(h, cudaStreamSynchronize(h->stream));
-    if (h->timing) {
-        rc = resolve_timing(h);
-        if (rc) return rc;
-    }
-    if (ms) {
-        ms[0] = h->t_p_ms;
-        ms[1] = h->t_u_ms;
-        ms[2] = h->t_small_ms;
-    }
-    if (launches) {
-        launches[0] = h->n_p;
-        launches[1] = h->n_u;
-        launches[2] = h->n_small;
-    }
-    h->t_p_ms = h->t_u_ms = h->t_small_ms = 0.0;
-    h->n_p = h->n_u = h->n_small = 0;
-    return HL_OK;
-}
-
+// ---------------------------------------------------------------------------
+// state copies between the host layout and the slot-major device layout
 static int copy_in(hl_solver *h, const double *p, const double *u, cudaMemcpyKind kind)
 {
-    const size_t pb = (size_t)h->nnode * h->nq * sizeof(double);
-    double *sp = h->staging, *su = h->staging + (size_t)h->nnode * h->nq;
-    HL_CK(h, cudaMemcpyAsync(sp, p, pb, kind, h->stream));
-    HL_CK(h, cudaMemcpyAsync(su, u, pb * h->dim, kind, h->stream));
-    HL_CK(h, launch_aos_to_soa(sp, h->p, 1, h->nnode, (int)h->nq, h->stream));
-    HL_CK(h, launch_aos_to_soa(su, h->u, h->dim, h->nnode, (int)h->nq, h->stream));
+    double *sp = h->staging, *su = h->staging + h->p_elems;
+    HL_CK(h, cudaMemcpyAsync(sp, p, (size_t)h->p_elems * sizeof(double), kind, h->stream));
+    HL_CK(h, cudaMemcpyAsync(su, u, (size_t)h->u_elems * sizeof(double), kind, h->stream));
+    for (const Shot &s : h->shots) {
+        HL_CK(h, launch_aos_to_soa(sp + s.p_off, h->p + s.p_off, 1, s.nnode, (int)h->nq, h->stream));
+        HL_CK(h, launch_aos_to_soa(su + s.u_off, h->u + s.u_off, h->dim, s.nnode, (int)h->nq, h->stream));
+    }
     HL_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     h->steps = 0;
     return HL_OK;
@@ -308,8 +425,11 @@ extern "C" int hl_get_fields_device(hl_solver *h, double *p_dev, double *u_dev)
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (p_dev) HL_CK(h, launch_soa_to_aos(h->p, p_dev, 1, h->nnode, (int)h->nq, h->stream));
-    if (u_dev) HL_CK(h, launch_soa_to_aos(h->u, u_dev, h->dim, h->nnode, (int)h->nq, h->stream));
+    for (const Shot &s : h->shots) {
+        if (p_dev) HL_CK(h, launch_soa_to_aos(h->p + s.p_off, p_dev + s.p_off, 1, s.nnode, (int)h->nq, h->stream));
+        if (u_dev)
+            HL_CK(h, launch_soa_to_aos(h->u + s.u_off, u_dev + s.u_off, h->dim, s.nnode, (int)h->nq, h->stream));
+    }
     return HL_OK;
 }
 
@@ -317,18 +437,13 @@ extern "C" int hl_get_fields(hl_solver *h, double *p, double *u, double *t_p, do
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    const size_t pb = (size_t)h->nnode * h->nq * sizeof(double);
-    double *sp = h->staging, *su = h->staging + (size_t)h->nnode * h->nq;
-    if (p) {
-        HL_CK(h, launch_soa_to_aos(h->p, sp, 1, h->nnode, (int)h->nq, h->stream));
-        HL_CK(h, cudaMemcpyAsync(p, sp, pb, cudaMemcpyDeviceToHost, h->stream));
-    }
-    if (u) {
-        HL_CK(h, launch_soa_to_aos(h->u, su, h->dim, h->nnode, (int)h->nq, h->stream));
-        HL_CK(h, cudaMemcpyAsync(u, su, pb * h->dim, cudaMemcpyDeviceToHost, h->stream));
-    }
-    if (t_p) *t_p = (double)h->steps * h->dt;
-    if (t_u) *t_u = ((double)h->steps + 0.5) * h->dt;
+    double *sp = h->staging, *su = h->staging + h->p_elems;
+    rc = hl_get_fields_device(h, p ? sp : nullptr, u ? su : nullptr);
+    if (rc) return rc;
+    if (p) HL_CK(h, cudaMemcpyAsync(p, sp, (size_t)h->p_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (u) HL_CK(h, cudaMemcpyAsync(u, su, (size_t)h->u_elems * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (t_p) *t_p = (double)h->steps * h->shots[0].dt;
+    if (t_u) *t_u = ((double)h->steps + 0.5) * h->shots[0].dt;
     return read_status(h, true);
 }
 
@@ -339,46 +454,103 @@ extern "C" int hl_sync(hl_solver *h)
     return read_status(h, true);
 }
 
+// ---------------------------------------------------------------------------
+static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_steps)
+{
+    LaunchFp64 a;
+    a.m = h->m;
+    for (int k = 0; k < 3; ++k) a.n[k] = (int)h->shots[0].n[k];
+    a.nnode = h->shots[0].nnode;
+    a.coef_host = h->coef.data();
+    a.coef_dev = h->coef_dev;
+    a.per_shot_coef = h->per_shot_coef;
+    a.shots = h->shot_desc_dev;
+    a.n_shots = (int)h->shots.size();
+    a.total_tiles = h->total_tiles;
+    a.tx = h->dim == 1 ? kTiles[h->tile][0] * kTiles[h->tile][1] : kTiles[h->tile][0];
+    a.ty = h->dim == 1 ? 1 : kTiles[h->tile][1];
+    a.P = P;
+    a.U = U;
+    a.nsteps = n_steps;
+    a.stream = h->stream;
+    a.status = h->status;
+    a.path = h->path;
+    a.ev = nullptr;
+    a.used_small = nullptr;
+    a.src = &h->src;
+    a.step0 = h->steps;
+    a.precision = h->precision;
+    return a;
+}
+
+static cudaError_t dispatch(int dim, const LaunchFp64 &a)
+{
+    if (a.precision != HL_FP64) {
+        switch (dim) {
+        case 1: return launch_mixed_d1(a);
+        case 2: return launch_mixed_d2(a);
+        case 3: return launch_mixed_d3(a);
+        }
+        return cudaErrorInvalidValue;
+    }
+    switch (dim) {
+    case 1: return launch_fp64_d1(a);
+    case 2: return launch_fp64_d2(a);
+    case 3: return launch_fp64_d3(a);
+    }
+    return cudaErrorInvalidValue;
+}
+
 extern "C" int hl_step(hl_solver *h, int64_t n_steps)
 {
     int rc = check_usable(h);
     if (rc) return rc;
     if (n_steps < 0) return set_err(h, HL_EINVAL, "n_steps must be >= 0");
     if (n_steps == 0) return HL_OK;
-    LaunchFp64 a;
-    a.m = h->m;
-    for (int k = 0; k < 3; ++k) a.n[k] = (int)h->n[k];
-    a.nnode = h->nnode;
-    a.coef_host = h->coef.data();
-    a.coef_dev = h->coef_dev;
-    a.P = h->p;
-    a.U = h->u;
-    a.nsteps = n_steps;
-    a.stream = h->stream;
-    a.status = h->status;
-    a.path = h->path;
-    a.src = h->src;
-    a.step0 = h->steps;
-    a.ev = nullptr;
+    LaunchFp64 a = launch_args(h, h->p, h->u, n_steps);
+    if (h->use_graph) {
+        // the whole call as one CUDA graph, launched on a private stream that is
+        // ordered after, and joined back into, the handle's stream
+        if (h->graph_exec) {
+            HL_CK(h, cudaStreamSynchronize(h->cap_stream));
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        a.stream = h->cap_stream;
+        a.path = PATH_GRID;
+        HL_CK(h, cudaEventRecord(h->ev_fork, h->stream));
+        HL_CK(h, cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0));
+        HL_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e = dispatch(h->dim, a);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail_cuda(h, e != cudaSuccess ? e : e2, "hl_step graph capture");
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess) return fail_cuda(h, e3, "cudaGraphInstantiate");
+        HL_CK(h, cudaGraphLaunch(h->graph_exec, h->cap_stream));
+        HL_CK(h, cudaEventRecord(h->ev_join, h->cap_stream));
+        HL_CK(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        h->steps += n_steps;
+        return HL_OK;
+    }
     bool used_small = false;
     a.used_small = &used_small;
     size_t first = 0;
     if (h->timing) {
         const size_t need = h->ev_used + 2 * (size_t)n_steps + 1;
         while (h->ev_pool.size() < need) {
-            cudaEvent_t e;
-            HL_CK(h, cudaEventCreate(&e));
-            h->ev_pool.push_back(e);
+            cudaEvent_t ev;
+            HL_CK(h, cudaEventCreate(&ev));
+            h->ev_pool.push_back(ev);
         }
         first = h->ev_used;
         a.ev = h->ev_pool.data() + first;
     }
-    cudaError_t e = cudaSuccess;
-    switch (h->dim) {
-    case 1: e = launch_fp64_d1(a); break;
-    case 2: e = launch_fp64_d2(a); break;
-    case 3: e = launch_fp64_d3(a); break;
-    }
+    const cudaError_t e = dispatch(h->dim, a);
     if (e != cudaSuccess) return fail_cuda(h, e, "hl_step kernel launch");
     if (h->timing) {
         h->pending.push_back({first, n_steps, used_small});
@@ -388,47 +560,152 @@ extern "C" int hl_step(hl_solver *h, int64_t n_steps)
     return HL_OK;
 }
 
+extern "C" int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->timing) {
+        rc = resolve_timing(h);
+        if (rc) return rc;
+    }
+    if (ms) {
+        ms[0] = h->t_p_ms;
+        ms[1] = h->t_u_ms;
+        ms[2] = h->t_small_ms;
+    }
+    if (launches) {
+        launches[0] = h->n_p;
+        launches[1] = h->n_u;
+        launches[2] = h->n_small;
+    }
+    h->t_p_ms = h->t_u_ms = h->t_small_ms = 0.0;
+    h->n_p = h->n_u = h->n_small = 0;
+    return HL_OK;
+}
+
+extern "C" int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile, double *ms_per_tile)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (steps_per_trial < 1) return set_err(h, HL_EINVAL, "steps_per_trial must be >= 1");
+    // trials run on scratch copies of the state, so the solution is not advanced
+    double *sp = nullptr, *su = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t pb = (size_t)h->p_elems * sizeof(double);
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    cudaError_t e;
+    if ((e = cudaMalloc(&sp, pb)) != cudaSuccess || (e = cudaMalloc(&su, pb * h->dim)) != cudaSuccess) {
+        if (sp) cudaFree(sp);
+        cudaGetLastError();
+        return set_err(h, HL_ENOMEM, std::string("autotune scratch: ") + cudaGetErrorString(e));
+    }
+    HL_CK(h, cudaEventCreate(&e0));
+    HL_CK(h, cudaEventCreate(&e1));
+    const int keep_tile = h->tile;
+    int best = keep_tile;
+    double best_ms = 1e300;
+    for (int t = 0; t < kNumTiles; ++t) {
+        if (ms_per_tile) ms_per_tile[t] = -1.0;
+        if (h->dim == 1 && kTiles[t][1] != 1) continue;  // 1D folds tiles into x
+        rc = build_tiles(h, t);
+        if (rc) break;
+        HL_CK(h, cudaMemcpyAsync(sp, h->p, pb, cudaMemcpyDeviceToDevice, h->stream));
+        HL_CK(h, cudaMemcpyAsync(su, h->u, pb * h->dim, cudaMemcpyDeviceToDevice, h->stream));
+        LaunchFp64 a = launch_args(h, sp, su, 1);
+        a.path = PATH_GRID;
+        a.src = nullptr;
+        HL_CK(h, dispatch(h->dim, a));  // warm-up
+        a.nsteps = steps_per_trial;
+        HL_CK(h, cudaEventRecord(e0, h->stream));
+        HL_CK(h, dispatch(h->dim, a));
+        HL_CK(h, cudaEventRecord(e1, h->stream));
+        HL_CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HL_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms_per_tile) ms_per_tile[t] = ms / steps_per_trial;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    HL_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));  // trial data may be anything
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sp);
+    cudaFree(su);
+    if (rc) {
+        build_tiles(h, keep_tile);
+        return rc;
+    }
+    rc = build_tiles(h, best);
+    if (rc) return rc;
+    if (best_tile) *best_tile = best;
+    return HL_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int hl_set_sources(hl_solver *h, const double *x0, const double *sigma, const double *f0,
+                              const double *amp)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (!x0 || !sigma || !f0 || !amp) return set_err(h, HL_EINVAL, "NULL source argument");
+    const int ns = (int)h->shots.size();
+    for (int s = 0; s < ns; ++s) {
+        if (amp[s] == 0.0) continue;
+        for (int k = 0; k < h->dim; ++k)
+            if (!std::isfinite(x0[(size_t)s * h->dim + k])) return set_err(h, HL_EINVAL, "x0 must be finite");
+        if (!(sigma[s] > 0.0) || !std::isfinite(sigma[s])) return set_err(h, HL_EINVAL, "sigma must be finite and > 0");
+        if (!(f0[s] > 0.0) || !std::isfinite(f0[s])) return set_err(h, HL_EINVAL, "f0 must be finite and > 0");
+        if (!std::isfinite(amp[s])) return set_err(h, HL_EINVAL, "amp must be finite");
+    }
+    std::vector<int> node, shot;
+    std::vector<double> table;
+    for (int s = 0; s < ns; ++s) {
+        if (amp[s] == 0.0) continue;
+        std::vector<int> nd;
+        std::vector<double> tb;
+        if (!build_source_table(h->dim, h->m, h->shots[s].n, x0 + (size_t)s * h->dim, sigma[s], nd, tb))
+            return set_err(h, HL_EINVAL, "source box too large");
+        node.insert(node.end(), nd.begin(), nd.end());
+        shot.insert(shot.end(), nd.size(), s);
+        table.insert(table.end(), tb.begin(), tb.end());
+        if (node.size() >= ((size_t)1 << 30)) return set_err(h, HL_EINVAL, "source boxes too large");
+    }
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->cap_stream) HL_CK(h, cudaStreamSynchronize(h->cap_stream));
+    free_source(h);
+    if (node.empty()) return HL_OK;
+    HL_CK(h, cudaMalloc(&h->src_node, node.size() * sizeof(int)));
+    HL_CK(h, cudaMalloc(&h->src_shot, shot.size() * sizeof(int)));
+    HL_CK(h, cudaMalloc(&h->src_table, table.size() * sizeof(double)));
+    HL_CK(h, cudaMemcpy(h->src_node, node.data(), node.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HL_CK(h, cudaMemcpy(h->src_shot, shot.data(), shot.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HL_CK(h, cudaMemcpy(h->src_table, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice));
+    h->src.active = true;
+    h->src.n_entries = (int)node.size();
+    h->src.node = h->src_node;
+    h->src.shot = h->src_shot;
+    h->src.table = h->src_table;
+    h->src.dt.resize(ns);
+    h->src.amp.assign(amp, amp + ns);
+    h->src.f0.assign(f0, f0 + ns);
+    for (int s = 0; s < ns; ++s) h->src.dt[s] = h->shots[s].dt;
+    return HL_OK;
+}
+
 extern "C" int hl_set_source(hl_solver *h, const double *x0, double sigma, double f0, double amp)
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (amp == 0.0) {
-        HL_CK(h, cudaStreamSynchronize(h->stream));
-        if (h->src_nodes) cudaFree(h->src_nodes);
-        if (h->src_table) cudaFree(h->src_table);
-        h->src_nodes = nullptr;
-        h->src_table = nullptr;
-        h->src = SourceDesc();
-        return HL_OK;
-    }
-    if (!x0) return set_err(h, HL_EINVAL, "x0 is NULL");
-    for (int k = 0; k < h->dim; ++k)
-        if (!std::isfinite(x0[k])) return set_err(h, HL_EINVAL, "x0 must be finite");
-    if (!(sigma > 0.0) || !std::isfinite(sigma)) return set_err(h, HL_EINVAL, "sigma must be finite and > 0");
-    if (!(f0 > 0.0) || !std::isfinite(f0)) return set_err(h, HL_EINVAL, "f0 must be finite and > 0");
-    if (!std::isfinite(amp)) return set_err(h, HL_EINVAL, "amp must be finite");
-    std::vector<int> nodes;
-    std::vector<double> table;
-    if (!build_source_table(h->dim, h->m, h->n, x0, sigma, nodes, table))
-        return set_err(h, HL_EINVAL, "source box too large");
-    HL_CK(h, cudaStreamSynchronize(h->stream));
-    if (h->src_nodes) cudaFree(h->src_nodes);
-    if (h->src_table) cudaFree(h->src_table);
-    h->src_nodes = nullptr;
-    h->src_table = nullptr;
-    h->src = SourceDesc();
-    HL_CK(h, cudaMalloc(&h->src_nodes, nodes.size() * sizeof(int)));
-    HL_CK(h, cudaMalloc(&h->src_table, table.size() * sizeof(double)));
-    HL_CK(h, cudaMemcpy(h->src_nodes, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
-    HL_CK(h, cudaMemcpy(h->src_table, table.data(), table.size() * sizeof(double), cudaMemcpyHostToDevice));
-    h->src.active = true;
-    h->src.nb = (int)nodes.size();
-    h->src.nodes = h->src_nodes;
-    h->src.table = h->src_table;
-    h->src.dt = h->dt;
-    h->src.amp = amp;
-    h->src.f0 = f0;
-    return HL_OK;
+    if (!x0 && amp != 0.0) return set_err(h, HL_EINVAL, "x0 is NULL");
+    const size_t ns = h->shots.size();
+    std::vector<double> xs(ns * h->dim, 0.0), sg(ns, sigma), ff(ns, f0), aa(ns, amp);
+    for (size_t s = 0; s < ns; ++s)
+        for (int k = 0; k < h->dim; ++k) xs[s * h->dim + k] = x0 ? x0[k] : 0.0;
+    return hl_set_sources(h, xs.data(), sg.data(), ff.data(), aa.data());
 }
 
 extern "C" int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev)
@@ -437,7 +714,7 @@ extern "C" int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev)
     if (rc) return rc;
     if (!p_dev && !u_dev) {
         HL_CK(h, cudaStreamSynchronize(h->stream));
-        const size_t pb = (size_t)h->nnode * h->nq * sizeof(double);
+        const size_t pb = (size_t)h->p_elems * sizeof(double);
         HL_CK(h, cudaMemset(h->p_own, 0, pb));
         HL_CK(h, cudaMemset(h->u_own, 0, pb * h->dim));
         h->p = h->p_own;
@@ -454,9 +731,22 @@ extern "C" int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev)
 extern "C" int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps)
 {
     if (!h) return set_err(nullptr, HL_EINVAL, "null handle");
-    if (nnode) *nnode = h->nnode;
+    int64_t tot = 0;
+    for (const Shot &s : h->shots) tot += s.nnode;
+    if (nnode) *nnode = tot;
     if (nq) *nq = h->nq;
     if (steps) *steps = h->steps;
+    return HL_OK;
+}
+
+extern "C" int hl_operator_table(int dim, int m, const double *lam, double *out)
+{
+    if (dim < 1 || dim > 3 || m < 0 || m > 6 || !lam || !out) return set_err(nullptr, HL_EINVAL, "bad arguments");
+    double l3[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < dim; ++k) l3[k] = lam[k];
+    std::vector<double> c;
+    if (!build_operator(dim, m, l3, c)) return set_err(nullptr, HL_EINVAL, "operator construction failed");
+    std::memcpy(out, c.data(), c.size() * sizeof(double));
     return HL_OK;
 }
 

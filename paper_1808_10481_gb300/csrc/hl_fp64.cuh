@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hl_internal.h"
+
 namespace hl {
 
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
@@ -150,8 +152,10 @@ __device__ __forceinline__ void report_nonfinite(bool bad, unsigned *status)
 }
 
 // ---------------------------------------------------------------------------
-// p-half at one primal node: P[s] += sum_i sum_l coef(i,l,s) * bfly_i,l[pattern]
+// p-half at one primal node: out[s] += sum_i sum_l coef(i,l,s) * bfly_i,l[pattern]
 // (the host stores the coefficients already negated: p_new = p_old - series).
+// Callers start out[] at zero and add the node's own value last, so the
+// increment is summed at its own magnitude before the single final rounding.
 // Loads go through `ld(comp, slot, vertex_node)`.
 template <int D, int M, class C, class Ld>
 __device__ __forceinline__ void p_node(const C &coef, const Ld &ld, const int *vtx, double *out)
@@ -219,53 +223,111 @@ struct SharedLd {
 };
 
 // ---------------------------------------------------------------------------
-// Grid kernels: one launch per half-step.
-template <int D, int M, class C>
-__global__ void __launch_bounds__(128) k_p_half(const double *__restrict__ U, double *__restrict__ P, GridDesc g,
-                                                C coef, unsigned *status)
+// Grid kernels: one launch per half-step over a flattened list of tiles.
+// A tile is blockDim.x x blockDim.y nodes of one shot (x-fastest); the shot
+// table maps the block index to its shot, so one launch covers any number of
+// independent grids (a single solve is a batch of one).
+
+// coefficient providers: one table in the parameter bank for every shot, or a
+// per-shot table in global memory
+template <int D, int M>
+struct CoefParam {
+    CoefArg<D, M, Shape<D, M>::kParam> c;
+    __device__ __forceinline__ const CoefArg<D, M, Shape<D, M>::kParam> &at(int) const { return c; }
+};
+template <int D, int M>
+struct CoefShots {
+    const double *__restrict__ base;   // n_shots tables of NCOEF doubles
+    __device__ __forceinline__ CoefArg<D, M, false> at(int shot) const
+    {
+        return CoefArg<D, M, false>{base + (int64_t)shot * Shape<D, M>::NCOEF};
+    }
+};
+
+// Locate this block's shot and node; false if the thread is outside the grid.
+template <int D>
+__device__ __forceinline__ bool tile_node(const ShotDesc *__restrict__ shots, int n_shots, int &shot, ShotDesc &sd,
+                                          int64_t &node)
+{
+    const int tile = blockIdx.x;
+    int lo = 0, hi = n_shots - 1;
+    while (lo < hi) {  // last shot with tile_begin <= tile
+        const int mid = (lo + hi + 1) >> 1;
+        if (shots[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    shot = lo;
+    sd = shots[lo];
+    int t = tile - sd.tile_begin;
+    const int tx = t % sd.tiles[0];
+    t /= sd.tiles[0];
+    const int ty = t % sd.tiles[1];
+    const int tz = t / sd.tiles[1];
+    const int ix = tx * blockDim.x + threadIdx.x;
+    const int iy = ty * blockDim.y + threadIdx.y;
+    if (ix >= sd.n[0] || iy >= sd.n[1] || tz >= sd.n[2]) return false;
+    node = ix + (int64_t)sd.n[0] * (iy + (int64_t)sd.n[1] * tz);
+    return true;
+}
+
+template <int D, int M, class CP>
+__global__ void __launch_bounds__(256) k_p_half(const double *__restrict__ U, double *__restrict__ P,
+                                                const ShotDesc *__restrict__ shots, int n_shots, CP cp,
+                                                unsigned *status)
 {
     using S = Shape<D, M>;
-    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= g.nnode) return;
+    int shot;
+    ShotDesc sd;
+    int64_t node;
+    if (!tile_node<D>(shots, n_shots, shot, sd, node)) return;
+    const GridDesc g{{sd.n[0], sd.n[1], sd.n[2]}, sd.nnode};
+    const double *Us = U + sd.u_off;
+    double *Ps = P + sd.p_off;
     int vtx[S::NV];
     vertex_nodes<D>(g, node, -1, vtx);
     double out[S::NQ];
 #pragma unroll
-    for (int s = 0; s < S::NQ; ++s) out[s] = P[(int64_t)s * g.nnode + node];
-    GlobalLd ld{U, g.nnode, S::NQ};
-    p_node<D, M>(coef, ld, vtx, out);
+    for (int s = 0; s < S::NQ; ++s) out[s] = 0.0;
+    GlobalLd ld{Us, g.nnode, S::NQ};
+    p_node<D, M>(cp.at(shot), ld, vtx, out);
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < S::NQ; ++s) {
-        P[(int64_t)s * g.nnode + node] = out[s];
-        bad |= !isfinite(out[s]);
+        const double v = Ps[(int64_t)s * g.nnode + node] + out[s];
+        Ps[(int64_t)s * g.nnode + node] = v;
+        bad |= !isfinite(v);
     }
     report_nonfinite(bad, status);
 }
 
-template <int D, int M, int I0, int NI, class C>
-__global__ void __launch_bounds__(128) k_u_half(const double *__restrict__ P, double *__restrict__ U, GridDesc g,
-                                                C coef, unsigned *status)
+template <int D, int M, int I0, int NI, class CP>
+__global__ void __launch_bounds__(256) k_u_half(const double *__restrict__ P, double *__restrict__ U,
+                                                const ShotDesc *__restrict__ shots, int n_shots, CP cp,
+                                                unsigned *status)
 {
     using S = Shape<D, M>;
-    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= g.nnode) return;
+    int shot;
+    ShotDesc sd;
+    int64_t node;
+    if (!tile_node<D>(shots, n_shots, shot, sd, node)) return;
+    const GridDesc g{{sd.n[0], sd.n[1], sd.n[2]}, sd.nnode};
+    const double *Ps = P + sd.p_off;
+    double *Us = U + sd.u_off;
     int vtx[S::NV];
     vertex_nodes<D>(g, node, 0, vtx);
     double out[NI * S::NQ];
 #pragma unroll
-    for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-        for (int s = 0; s < S::NQ; ++s) out[ii * S::NQ + s] = U[(int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node];
-    GlobalLd ld{P, g.nnode, S::NQ};
-    u_node<D, M, I0, NI>(coef, ld, vtx, out);
+    for (int e = 0; e < NI * S::NQ; ++e) out[e] = 0.0;
+    GlobalLd ld{Ps, g.nnode, S::NQ};
+    u_node<D, M, I0, NI>(cp.at(shot), ld, vtx, out);
     bool bad = false;
 #pragma unroll
     for (int ii = 0; ii < NI; ++ii)
 #pragma unroll
         for (int s = 0; s < S::NQ; ++s) {
-            U[(int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node] = out[ii * S::NQ + s];
-            bad |= !isfinite(out[ii * S::NQ + s]);
+            double *dst = Us + (int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node;
+            const double v = *dst + out[ii * S::NQ + s];
+            *dst = v;
+            bad |= !isfinite(v);
         }
     report_nonfinite(bad, status);
 }
@@ -279,12 +341,13 @@ __device__ __forceinline__ void small_u_split(const C &coef, const Ld &ld, const
         using S = Shape<D, M>;
         double out[S::NQ];
 #pragma unroll
-        for (int s = 0; s < S::NQ; ++s) out[s] = sU[(I * S::NQ + s) * nn + node];
+        for (int s = 0; s < S::NQ; ++s) out[s] = 0.0;
         u_node<D, M, I, 1>(coef, ld, vtx, out);
 #pragma unroll
         for (int s = 0; s < S::NQ; ++s) {
-            sU[(I * S::NQ + s) * nn + node] = out[s];
-            bad |= !isfinite(out[s]);
+            const double v = sU[(I * S::NQ + s) * nn + node] + out[s];
+            sU[(I * S::NQ + s) * nn + node] = v;
+            bad |= !isfinite(v);
         }
         small_u_split<D, M, I + 1>(coef, ld, vtx, sU, nn, node, bad);
     }
@@ -314,12 +377,13 @@ __global__ void __launch_bounds__(256) k_small(double *__restrict__ P, double *_
             vertex_nodes<D>(g, node, -1, vtx);
             double out[S::NQ];
 #pragma unroll
-            for (int s = 0; s < S::NQ; ++s) out[s] = sP[s * nn + node];
+            for (int s = 0; s < S::NQ; ++s) out[s] = 0.0;
             p_node<D, M>(coef, ldU, vtx, out);
 #pragma unroll
             for (int s = 0; s < S::NQ; ++s) {
-                sP[s * nn + node] = out[s];
-                bad |= !isfinite(out[s]);
+                const double v = sP[s * nn + node] + out[s];
+                sP[s * nn + node] = v;
+                bad |= !isfinite(v);
             }
         }
         __syncthreads();
@@ -329,12 +393,13 @@ __global__ void __launch_bounds__(256) k_small(double *__restrict__ P, double *_
             if constexpr (S::kUFused) {
                 double out[D * S::NQ];
 #pragma unroll
-                for (int e = 0; e < D * S::NQ; ++e) out[e] = sU[e * nn + node];
+                for (int e = 0; e < D * S::NQ; ++e) out[e] = 0.0;
                 u_node<D, M, 0, D>(coef, ldP, vtx, out);
 #pragma unroll
                 for (int e = 0; e < D * S::NQ; ++e) {
-                    sU[e * nn + node] = out[e];
-                    bad |= !isfinite(out[e]);
+                    const double v = sU[e * nn + node] + out[e];
+                    sU[e * nn + node] = v;
+                    bad |= !isfinite(v);
                 }
             } else {
                 small_u_split<D, M, 0>(coef, ldP, vtx, sU, nn, node, bad);

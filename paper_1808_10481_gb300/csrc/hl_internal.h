@@ -8,34 +8,59 @@
 
 namespace hl {
 
+constexpr int kMaxShots = 256;  // shots per batched handle
+
 bool hermite_inverse_1d(int m, std::vector<double> &H);
 bool build_operator(int D, int m, const double lam[3], std::vector<double> &coef);
 void fp64_op_counts(int D, int m, double *fma_per_node_step, double *add_per_node_step);
 
-// Point source of the p-half (see hl_source.cu).
+// One grid of a launch (a single solve is a batch of one).
+struct ShotDesc {
+    int n[3];          // nodes per axis (1 for unused axes)
+    int tiles[3];      // tiles per axis: ceil(n0/TX), ceil(n1/TY), n2
+    int64_t nnode;     // n0*n1*n2
+    int64_t p_off;     // element offset of the shot's p block [q][node]
+    int64_t u_off;     // element offset of the shot's u block [comp][q][node]
+    int tile_begin;    // first tile of the shot in the launch
+    int pad;
+};
+
+// Per-step source weights dt_s * amp_s * R((n + 1/2) dt_s) of every shot.
+struct SourceWeights {
+    double w[kMaxShots];
+};
+
+// Point sources of the p-half (see hl_source.cu): one Gaussian box per shot.
 struct SourceDesc {
     bool active = false;
-    int nb = 0;                      // box nodes
-    const int *nodes = nullptr;      // device, node index of each box node
-    const double *table = nullptr;   // device, [q][box node] scaled Gaussian data
-    double dt = 0.0, amp = 0.0, f0 = 1.0;
+    int n_entries = 0;              // box nodes over all shots
+    const int *node = nullptr;      // device: shot-local node index of each entry
+    const int *shot = nullptr;      // device: shot of each entry
+    const double *table = nullptr;  // device: [entry][q] scaled Gaussian data
+    std::vector<double> dt, amp, f0;  // host, per shot (amp = 0: no source)
 };
 double ricker(double t, double f0);
 bool build_source_table(int dim, int m, const int64_t *n, const double *x0, double sigma,
                         std::vector<int> &nodes, std::vector<double> &table);
-cudaError_t launch_source(const SourceDesc &s, double *P, int64_t nnode, int nq, int64_t step, cudaStream_t st);
+cudaError_t launch_source(const SourceDesc &s, const ShotDesc *shots_dev, double *P, int nq, int64_t step,
+                          cudaStream_t st);
 
 enum KernelPath { PATH_AUTO = 0, PATH_SMALL = 1, PATH_GRID = 2 };
 
 // Arguments of one FP64 stepping call (n_steps full steps).
 struct LaunchFp64 {
     int m;
-    int n[3];
+    int n[3];                 // shape of shot 0 (the single-CTA path needs one shot)
     int64_t nnode;
-    const double *coef_host;  // dense (i, l, s) table, D*NQ*NQ doubles
-    const double *coef_dev;   // the same table in device memory
-    double *P;                // p[q][node]
-    double *U;                // u[comp][q][node]
+    const double *coef_host;  // single dense (i, l, s) table, D*NQ*NQ doubles
+    const double *coef_dev;   // device table(s): one, or n_shots back to back
+    bool per_shot_coef;       // use coef_dev + shot*NCOEF
+    const ShotDesc *shots;    // device shot table
+    int n_shots;
+    int total_tiles;
+    int tx, ty;               // tile (block) shape
+    double *P;                // p blocks [q][node] of every shot
+    double *U;                // u blocks [comp][q][node] of every shot
     int64_t nsteps;
     cudaStream_t stream;
     unsigned *status;         // device status word (bit 0: non-finite)
@@ -45,13 +70,17 @@ struct LaunchFp64 {
     // single-CTA path only ev[0] and ev[1] bracket the whole launch
     cudaEvent_t *ev;
     bool *used_small;         // set to whether the single-CTA path ran
-    SourceDesc src;           // point source injected after every p-half
+    const SourceDesc *src;    // point sources injected after every p-half (may be NULL)
     int64_t step0;            // index of the first step (source time)
+    int precision;            // HL_FP64 (0), HL_FP32 (1), HL_FP32_COMP (2)
 };
 
 cudaError_t launch_fp64_d1(const LaunchFp64 &a);
 cudaError_t launch_fp64_d2(const LaunchFp64 &a);
 cudaError_t launch_fp64_d3(const LaunchFp64 &a);
+cudaError_t launch_mixed_d1(const LaunchFp64 &a);  // precision 1 or 2, m <= 3
+cudaError_t launch_mixed_d2(const LaunchFp64 &a);
+cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 
 // host-layout <-> device-layout copies, ncomp blocks of [nnode][nq] <-> [nq][nnode]
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int ncomp, int64_t nnode, int nq, cudaStream_t st);

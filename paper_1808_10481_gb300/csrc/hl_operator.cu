@@ -30,51 +30,114 @@
 
 namespace hl {
 
-static double fact(int n)
+// Double-double arithmetic (a value is hi + lo with |lo| <= ulp(hi)/2), built
+// from the error-free transformations TwoSum (Knuth) and TwoProduct via fma
+// (Dekker), so the composed operator carries ~106-bit accuracy before its
+// single final rounding to binary64.  Composing W*H directly in binary64
+// leaves entry errors up to 1e-13 relative (heavy cancellation), which act as
+// a systematic perturbation of the scheme and grow with the step count.
+struct DD {
+    double hi, lo;
+};
+
+static DD dd(double x) { return {x, 0.0}; }
+
+static DD two_sum(double a, double b)
 {
-    double f = 1.0;
+    const double s = a + b;
+    const double bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+static DD fast_two_sum(double a, double b)
+{
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+
+static DD dd_add(DD a, DD b)
+{
+    const DD s = two_sum(a.hi, b.hi);
+    const DD t = two_sum(a.lo, b.lo);
+    DD r = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(r.hi, r.lo + t.lo);
+}
+
+static DD dd_neg(DD a) { return {-a.hi, -a.lo}; }
+
+static DD dd_mul(DD a, DD b)
+{
+    const double p = a.hi * b.hi;
+    const double e = std::fma(a.hi, b.hi, -p);
+    return fast_two_sum(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+
+static DD dd_div(DD a, DD b)
+{
+    const double q1 = a.hi / b.hi;
+    const DD r = dd_add(a, dd_neg(dd_mul(dd(q1), b)));
+    const double q2 = r.hi / b.hi;
+    const DD r2 = dd_add(r, dd_neg(dd_mul(dd(q2), b)));
+    const double q3 = r2.hi / b.hi;
+    return dd_add(fast_two_sum(q1, q2), dd(q3));
+}
+
+static DD dd_int(int64_t v)
+{
+    const double hi = (double)v;
+    return {hi, (double)(v - (int64_t)hi)};
+}
+
+static int64_t ifact(int n)
+{
+    int64_t f = 1;
     for (int k = 2; k <= n; ++k) f *= k;
     return f;
 }
 
-static double binom(int a, int l) { return fact(a) / (fact(l) * fact(a - l)); }
+static int64_t ibinom(int a, int l) { return ifact(a) / (ifact(l) * ifact(a - l)); }
 
+// H = [C^L; C^R]^{-1} by Gauss-Jordan with partial pivoting in double-double;
+// the exact inverse is dyadic (representable in binary64) for m <= 6, so the
+// final rounding returns it exactly.
 bool hermite_inverse_1d(int m, std::vector<double> &H)
 {
     const int A = 2 * m + 2;
-    std::vector<double> a(A * 2 * A, 0.0);  // augmented [A | I]
+    std::vector<DD> a((size_t)A * 2 * A, dd(0.0));  // augmented [A | I]
     for (int l = 0; l <= m; ++l) {
         for (int c = l; c < A; ++c) {
-            const double w = binom(c, l);
-            a[l * 2 * A + c] = w * std::pow(-0.5, c - l);
-            a[(m + 1 + l) * 2 * A + c] = w * std::pow(0.5, c - l);
+            const double w = (double)ibinom(c, l);
+            a[(size_t)l * 2 * A + c] = dd(w * std::ldexp((c - l) % 2 ? -1.0 : 1.0, -(c - l)));
+            a[(size_t)(m + 1 + l) * 2 * A + c] = dd(w * std::ldexp(1.0, -(c - l)));
         }
     }
-    for (int r = 0; r < A; ++r) a[r * 2 * A + A + r] = 1.0;
+    for (int r = 0; r < A; ++r) a[(size_t)r * 2 * A + A + r] = dd(1.0);
     for (int col = 0; col < A; ++col) {
         int piv = col;
         for (int r = col + 1; r < A; ++r)
-            if (std::fabs(a[r * 2 * A + col]) > std::fabs(a[piv * 2 * A + col])) piv = r;
-        if (a[piv * 2 * A + col] == 0.0) return false;
+            if (std::fabs(a[(size_t)r * 2 * A + col].hi) > std::fabs(a[(size_t)piv * 2 * A + col].hi)) piv = r;
+        if (a[(size_t)piv * 2 * A + col].hi == 0.0) return false;
         if (piv != col)
-            for (int c = 0; c < 2 * A; ++c) std::swap(a[col * 2 * A + c], a[piv * 2 * A + c]);
-        const double inv = 1.0 / a[col * 2 * A + col];
-        for (int c = 0; c < 2 * A; ++c) a[col * 2 * A + c] *= inv;
+            for (int c = 0; c < 2 * A; ++c) std::swap(a[(size_t)col * 2 * A + c], a[(size_t)piv * 2 * A + c]);
+        const DD pv = a[(size_t)col * 2 * A + col];
+        for (int c = 0; c < 2 * A; ++c) a[(size_t)col * 2 * A + c] = dd_div(a[(size_t)col * 2 * A + c], pv);
         for (int r = 0; r < A; ++r) {
             if (r == col) continue;
-            const double f = a[r * 2 * A + col];
-            if (f == 0.0) continue;
-            for (int c = 0; c < 2 * A; ++c) a[r * 2 * A + c] -= f * a[col * 2 * A + c];
+            const DD f = a[(size_t)r * 2 * A + col];
+            if (f.hi == 0.0) continue;
+            for (int c = 0; c < 2 * A; ++c)
+                a[(size_t)r * 2 * A + c] = dd_add(a[(size_t)r * 2 * A + c], dd_neg(dd_mul(f, a[(size_t)col * 2 * A + c])));
         }
     }
-    H.assign(A * A, 0.0);
+    H.assign((size_t)A * A, 0.0);
     for (int r = 0; r < A; ++r)
-        for (int c = 0; c < A; ++c) H[r * A + c] = a[r * 2 * A + A + c];
+        for (int c = 0; c < A; ++c) H[(size_t)r * A + c] = a[(size_t)r * 2 * A + A + c].hi;
     return true;
 }
 
-// Dense table coef[(i*NQ + l)*NQ + s] (negated series operator), NQ = (m+1)^D.
-// Returns false if the structural-zero rule the kernels rely on fails.
+// Dense table coef[(i*NQ + l)*NQ + s] (negated series operator), NQ = (m+1)^D,
+// composed in double-double and rounded once.  Returns false if the
+// structural-zero rule the kernels rely on fails.
 bool build_operator(int D, int m, const double lam[3], std::vector<double> &coef)
 {
     const int n = m + 1, A = 2 * m + 2;
@@ -82,46 +145,63 @@ bool build_operator(int D, int m, const double lam[3], std::vector<double> &coef
     for (int k = 0; k < D; ++k) NQ *= n;
     std::vector<double> H;
     if (!hermite_inverse_1d(m, H)) return false;
-    coef.assign((size_t)D * NQ * NQ, 0.0);
-    double maxabs = 0.0;
+    // lam_k^e in double-double, e = 0..2m+1
+    std::vector<DD> lp[3];
+    for (int k = 0; k < D; ++k) {
+        lp[k].assign(A, dd(1.0));
+        for (int e = 1; e < A; ++e) lp[k][e] = dd_mul(lp[k][e - 1], dd(lam[k]));
+    }
+    std::vector<DD> acc((size_t)D * NQ * NQ, dd(0.0));
     for (int i = 0; i < D; ++i) {
         for (int s = 0; s < NQ; ++s) {
             int sv[3] = {0, 0, 0};
             for (int k = 0, t = s; k < D; ++k, t /= n) sv[k] = t % n;
-            // enumerate b with 2 b_j + s_j + [j==i] <= 2m+1
             int bmax[3] = {0, 0, 0};
-            for (int k = 0; k < D; ++k) bmax[k] = (2 * m + 1 - sv[k] - (k == i ? 1 : 0)) / 2;
             bool any = true;
-            for (int k = 0; k < D; ++k)
-                if (sv[k] + (k == i ? 1 : 0) > 2 * m + 1) any = false;
+            for (int k = 0; k < D; ++k) {
+                const int t0 = sv[k] + (k == i ? 1 : 0);
+                if (t0 > 2 * m + 1) any = false;
+                bmax[k] = (2 * m + 1 - t0) / 2;
+            }
             if (!any) continue;
             for (int b2 = 0; b2 <= (D > 2 ? bmax[2] : 0); ++b2)
                 for (int b1 = 0; b1 <= (D > 1 ? bmax[1] : 0); ++b1)
                     for (int b0 = 0; b0 <= bmax[0]; ++b0) {
                         const int b[3] = {b0, b1, b2};
                         const int K = b0 + b1 + b2;
-                        int a[3];
-                        double w = 2.0 / fact(2 * K + 1) * fact(K);
+                        int a[3] = {0, 0, 0};
+                        // W = 2 K!/(2K+1)! * prod_k [a_k!/(s_k! b_k!)] lam_k^(a_k - s_k)
+                        DD w = dd_div(dd_int(2 * ifact(K)), dd_int(ifact(2 * K + 1)));
                         for (int k = 0; k < D; ++k) {
                             a[k] = sv[k] + 2 * b[k] + (k == i ? 1 : 0);
-                            w *= fact(a[k]) / (fact(sv[k]) * fact(b[k])) * std::pow(lam[k], a[k] - sv[k]);
+                            // a_k!/s_k! is an integer (a_k >= s_k) below 2^53
+                            w = dd_mul(w, dd_div(dd_int(ifact(a[k]) / ifact(sv[k])), dd_int(ifact(b[k]))));
+                            w = dd_mul(w, lp[k][a[k] - sv[k]]);
                         }
                         for (int l = 0; l < NQ; ++l) {
-                            double h = 1.0;
-                            for (int k = 0, t = l; k < D; ++k, t /= n) h *= H[a[k] * A + (t % n)];
-                            coef[((size_t)i * NQ + l) * NQ + s] -= w * h;
+                            double h = 1.0;  // products of dyadic H entries: exact
+                            for (int k = 0, t = l; k < D; ++k, t /= n) h *= H[(size_t)a[k] * A + (t % n)];
+                            DD &c = acc[((size_t)i * NQ + l) * NQ + s];
+                            c = dd_add(c, dd_neg(dd_mul(w, dd(h))));
                         }
                     }
         }
     }
-    for (double v : coef) maxabs = std::fmax(maxabs, std::fabs(v));
+    coef.resize(acc.size());
+    double maxabs = 0.0;
+    for (size_t e = 0; e < acc.size(); ++e) {
+        coef[e] = acc[e].hi + acc[e].lo;
+        maxabs = std::fmax(maxabs, std::fabs(coef[e]));
+    }
     // the kernels skip entries the structural rule declares zero: verify it
     for (int i = 0; i < D; ++i)
         for (int l = 0; l < NQ; ++l)
             for (int s = 0; s < NQ; ++s)
-                if (!coef_nonzero(D, n, i, s, l) &&
-                    std::fabs(coef[((size_t)i * NQ + l) * NQ + s]) > 1e-13 * maxabs)
-                    return false;
+                if (!coef_nonzero(D, n, i, s, l)) {
+                    double &c = coef[((size_t)i * NQ + l) * NQ + s];
+                    if (std::fabs(c) > 1e-13 * maxabs) return false;
+                    c = 0.0;  // exact zero: only double-double residue remains here
+                }
     return true;
 }
 
@@ -137,7 +217,9 @@ void fp64_op_counts(int D, int m, double *fma_per_node_step, double *add_per_nod
             for (int s = 0; s < NQ; ++s) nz += coef_nonzero(D, n, i, s, l) ? 1 : 0;
     const double bfly = (double)D * (1 << D) * NQ;  // one butterfly over NQ slots
     *fma_per_node_step = 2.0 * nz;                  // p-half and u-half share the table
-    *add_per_node_step = bfly * D + bfly;           // p-half: D components; u-half: one field
+    // butterflies (p-half: D components; u-half: one field) plus the final
+    // addition of each increment to the node's own value
+    *add_per_node_step = bfly * D + bfly + (double)NQ * (1 + D);
 }
 
 }  // namespace hl

@@ -8,7 +8,7 @@
 //   p~_a += dt * amp * R((n + 1/2) dt) * g~_a,
 // g~_a = prod_k (h_k^{a_k}/a_k!) d^{a_k}/dx_k^{a_k} exp(-(x_k - x0_k)^2/(2 sigma^2)).
 // The table g~ is built once on the host over the box of nodes within
-// 10 sigma of x0 on every axis (g < exp(-50) outside), stored [q][box node].
+// 10 sigma of x0 on every axis (g < exp(-50) outside), stored [box node][q].
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -88,27 +88,35 @@ bool build_source_table(int dim, int m, const int64_t *n, const double *x0, doub
                 nodes[b] = (int)(idx[0][i0] + n[0] * ((int64_t)idx[1][i1] + n[1] * (int64_t)idx[2][i2]));
                 for (int64_t q = 0; q < nq; ++q) {
                     const int a0 = (int)(q % nqa), a1 = (int)((q / nqa) % nqa), a2 = (int)(q / (nqa * nqa));
-                    table[(size_t)q * nb + b] =
+                    table[b * (size_t)nq + q] =
                         fac[0][i0 * nqa + a0] * fac[1][i1 * nqa + a1] * fac[2][i2 * nqa + a2];
                 }
             }
     return true;
 }
 
-__global__ void k_source(double *__restrict__ P, int64_t nnode, int nq, const int *__restrict__ nodes,
-                         const double *__restrict__ table, int nb, double w)
+__global__ void k_source(double *__restrict__ P, const ShotDesc *__restrict__ shots, const int *__restrict__ node,
+                         const int *__restrict__ shot, const double *__restrict__ table, int ne, int nq,
+                         SourceWeights w)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const int node = nodes[b];
-    for (int q = 0; q < nq; ++q) P[(int64_t)q * nnode + node] += w * table[(int64_t)q * nb + b];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int s = shot[e];
+    const ShotDesc sd = shots[s];
+    double *Ps = P + sd.p_off + node[e];
+    for (int q = 0; q < nq; ++q) Ps[(int64_t)q * sd.nnode] += w.w[s] * table[(int64_t)e * nq + q];
 }
 
-cudaError_t launch_source(const SourceDesc &s, double *P, int64_t nnode, int nq, int64_t step, cudaStream_t st)
+cudaError_t launch_source(const SourceDesc &s, const ShotDesc *shots_dev, double *P, int nq, int64_t step,
+                          cudaStream_t st)
 {
-    if (!s.active) return cudaSuccess;
-    const double w = s.dt * s.amp * ricker(((double)step + 0.5) * s.dt, s.f0);
-    k_source<<<(s.nb + 127) / 128, 128, 0, st>>>(P, nnode, nq, s.nodes, s.table, s.nb, w);
+    if (!s.active || s.n_entries == 0) return cudaSuccess;
+    SourceWeights w;
+    const size_t ns = s.dt.size();
+    for (size_t i = 0; i < (size_t)kMaxShots; ++i)
+        w.w[i] = (i < ns && s.amp[i] != 0.0) ? s.dt[i] * s.amp[i] * ricker(((double)step + 0.5) * s.dt[i], s.f0[i])
+                                            : 0.0;
+    k_source<<<(s.n_entries + 127) / 128, 128, 0, st>>>(P, shots_dev, s.node, s.shot, s.table, s.n_entries, nq, w);
     return cudaGetLastError();
 }
 

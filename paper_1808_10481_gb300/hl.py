@@ -18,8 +18,14 @@ LIB_PATH = os.path.join(HERE, "_build", "libhl.so")
 
 HL_OK, HL_EINVAL, HL_ENOMEM, HL_ECUDA, HL_ETIMEOUT, HL_ENONFINITE, HL_ESTATE = 0, -1, -2, -3, -4, -5, -6
 HL_FP64 = 0
+HL_FP32 = 1
+HL_FP32_COMP = 2
 HL_OPT_KERNEL_PATH = 1
 HL_OPT_TIMING = 2
+HL_OPT_GRAPH = 3
+HL_OPT_TILE = 4
+HL_NUM_TILES = 8
+TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16)]
 CODE_NAMES = {0: "HL_OK", -1: "HL_EINVAL", -2: "HL_ENOMEM", -3: "HL_ECUDA", -4: "HL_ETIMEOUT",
               -5: "HL_ENONFINITE", -6: "HL_ESTATE"}
 
@@ -38,6 +44,8 @@ _D = ctypes.c_double
 # (name, restype, argtypes): mirrors include/hl.h
 _SIGNATURES = [
     ("hl_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, ctypes.POINTER(_P)]),
+    ("hl_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64),
+                                        ctypes.POINTER(_D), ctypes.POINTER(_P)]),
     ("hl_set_initial", ctypes.c_int, [_P, _P, _P]),
     ("hl_set_initial_device", ctypes.c_int, [_P, _P, _P]),
     ("hl_get_fields_device", ctypes.c_int, [_P, _P, _P]),
@@ -49,9 +57,13 @@ _SIGNATURES = [
     ("hl_set_stream", ctypes.c_int, [_P, _P]),
     ("hl_bind_device", ctypes.c_int, [_P, _P, _P]),
     ("hl_set_source", ctypes.c_int, [_P, ctypes.POINTER(_D), _D, _D, _D]),
+    ("hl_set_sources", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                       ctypes.POINTER(_D)]),
+    ("hl_autotune", ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D)]),
     ("hl_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
 ]
@@ -75,16 +87,21 @@ def load(path: str = LIB_PATH):
 
 @dataclass
 class Handle:
-    """Opaque solver pointer plus the sizes needed to marshal buffers."""
+    """Opaque solver pointer plus the sizes needed to marshal buffers.
+
+    For a batch, n_cells is a tuple of per-shot tuples and dt a tuple of floats."""
     ptr: ctypes.c_void_p
     dim: int
     m: int
     n_cells: tuple
     dt: float
+    n_shots: int = 1
 
     @property
     def nnode(self) -> int:
-        return int(np.prod(self.n_cells))
+        if self.n_shots == 1:
+            return int(np.prod(self.n_cells))
+        return int(sum(int(np.prod(c)) for c in self.n_cells))
 
     @property
     def nq(self) -> int:
@@ -134,6 +151,23 @@ def hl_create(dim: int, m: int, n_cells, dt: float) -> Handle:
     if rc != HL_OK:
         raise HLError(rc, lib.hl_last_error(None).decode(errors="replace"))
     return Handle(out, int(dim), int(m), tuple(int(x) for x in n_cells), float(dt))
+
+
+def hl_create_batch(dim: int, m: int, n_cells, dt) -> Handle:
+    """n_cells: sequence of per-shot node counts (each dim long); dt: per-shot steps."""
+    lib = load()
+    flat = [int(x) for c in n_cells for x in c]
+    ns = len(dt)
+    if len(flat) != ns * dim:
+        raise ValueError("n_cells must hold dim entries per shot")
+    nc = (_I64 * len(flat))(*flat)
+    dts = (_D * ns)(*[float(x) for x in dt])
+    out = _P()
+    rc = lib.hl_create_batch(int(dim), int(m), ns, nc, dts, ctypes.byref(out))
+    if rc != HL_OK:
+        raise HLError(rc, lib.hl_last_error(None).decode(errors="replace"))
+    return Handle(out, int(dim), int(m), tuple(tuple(int(x) for x in c) for c in n_cells),
+                  tuple(float(x) for x in dt), ns)
 
 
 def hl_set_initial(h: Handle, p, u) -> None:
@@ -203,6 +237,23 @@ def hl_set_source(h: Handle, x0, sigma: float, f0: float, amp: float) -> None:
     _check(h, load().hl_set_source(h.ptr, x, float(sigma), float(f0), float(amp)))
 
 
+def hl_set_sources(h: Handle, x0, sigma, f0, amp) -> None:
+    ns = h.n_shots
+    flat = [float(v) for row in x0 for v in row]
+    if len(flat) != ns * h.dim:
+        raise ValueError("x0 must hold dim coordinates per shot")
+    arr = lambda v: (_D * ns)(*[float(x) for x in v])
+    _check(h, load().hl_set_sources(h.ptr, (_D * len(flat))(*flat), arr(sigma), arr(f0), arr(amp)))
+
+
+def hl_autotune(h: Handle, steps_per_trial: int = 2):
+    """Returns (best tile index, [ms per step of each tile shape or -1])."""
+    best = ctypes.c_int()
+    ms = (_D * HL_NUM_TILES)()
+    _check(h, load().hl_autotune(h.ptr, int(steps_per_trial), ctypes.byref(best), ms))
+    return best.value, list(ms)
+
+
 def hl_set_precision(h: Handle, mode: int) -> None:
     _check(h, load().hl_set_precision(h.ptr, int(mode)))
 
@@ -218,6 +269,17 @@ def hl_kernel_times(h: Handle):
     _check(h, load().hl_kernel_times(h.ptr, ms, n))
     keys = ("p_half", "u_half", "small")
     return dict(zip(keys, list(ms))), dict(zip(keys, list(n)))
+
+
+def hl_operator_table(dim: int, m: int, lam) -> np.ndarray:
+    """The fused operator (dim, nq, nq) indexed [i, l, s]."""
+    nq = (m + 1) ** dim
+    out = np.empty(dim * nq * nq, dtype=np.float64)
+    lm = (_D * 3)(*([float(x) for x in lam] + [0.0] * (3 - len(lam))))
+    rc = load().hl_operator_table(int(dim), int(m), lm, out.ctypes.data_as(ctypes.POINTER(_D)))
+    if rc != HL_OK:
+        raise HLError(rc, hl_last_error(None))
+    return out.reshape(dim, nq, nq)
 
 
 def hl_op_counts(dim: int, m: int):

@@ -1,0 +1,80 @@
+"""Run one Hermite-leapfrog case through the C ABI and print its timing.
+
+  python -m paper_1808_10481_gb300.run_case --dim 2 --m 3 --n 512 --steps 200 [--warmup 3]
+
+The state lives on the device for the whole run; timing is CUDA events around
+hl_step.  Used for quick experiments and as the command profiled by ncu.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--m", type=int, default=3)
+    ap.add_argument("--n", type=int, nargs="+", default=[512])
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--cfl", type=float, default=0.9)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 single CTA, 2 grid launches")
+    ap.add_argument("--init", choices=["gaussian", "random", "zero"], default="random")
+    args = ap.parse_args(argv)
+
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import hl
+    from paper_1808_10481_gb300 import inputs as I
+
+    hl.load()
+    ncell = args.n * args.dim if len(args.n) == 1 else args.n
+    dt = I.cfl_dt(ncell, args.cfl)
+    if args.init == "gaussian":
+        st = I.gaussian_pulse(args.dim, args.m, ncell, dt, seed=args.seed)
+        p, u = st.p, st.u
+    elif args.init == "random":
+        st = I.random_state(args.dim, args.m, ncell, seed=args.seed)
+        p, u = st.p, st.u
+    else:
+        nq = (args.m + 1) ** args.dim
+        p = np.zeros((int(np.prod(ncell)), nq))
+        u = np.zeros((args.dim,) + p.shape)
+    h = hl.hl_create(args.dim, args.m, ncell, dt)
+    try:
+        stream = torch.cuda.current_stream()
+        hl.hl_set_stream(h, stream)
+        if args.path:
+            hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, args.path)
+        hl.hl_set_initial(h, p, u)
+        if args.warmup:
+            hl.hl_step(h, args.warmup)
+        hl.hl_sync(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hl.hl_step(h, args.steps)
+        e1.record(stream)
+        status = hl.hl_sync(h)
+        ms = e0.elapsed_time(e1)
+    finally:
+        hl.hl_destroy(h)
+    dof = (args.dim + 1) * (args.m + 1) ** args.dim * int(np.prod(ncell))
+    print(json.dumps({"dim": args.dim, "m": args.m, "n_cells": ncell, "steps": args.steps, "ms": ms,
+                      "ms_per_step": ms / max(args.steps, 1), "dof_updates_per_s": dof * args.steps / (ms / 1e3),
+                      "status": status}))
+    return 0 if status == hl.HL_OK else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,4 +92,68 @@ def test_kernel_sparsity_rule_matches_operator(d, m):
     fma, add = hl.hl_op_counts(d, m)
     nz = _butterflied_nnz(d, m, [0.45, 0.37, 0.29][:d])
     assert fma == 2 * nz                       # p-half and u-half use the same table
-    assert add == d * (1 << d) * (m + 1) ** d * (d + 1)
+    assert add == d * (1 << d) * (m + 1) ** d * (d + 1) + (m + 1) ** d * (d + 1)
+
+
+@pytest.mark.parametrize("args,fragment", [
+    ((2, 3, 0, [], []), "n_shots"),
+    ((2, 3, 257, [[8, 8]] * 257, [0.01] * 257), "n_shots"),
+    ((2, 4, 2, [[8, 8], [8, 8]], [0.01, 0.01]), "m <= 3"),
+    ((2, 3, 2, [[8, 8], [8, 1]], [0.01, 0.01]), ">= 2"),
+    ((2, 3, 2, [[8, 8], [16, 16]], [0.01, 0.07]), "min h"),
+])
+def test_batch_arguments_rejected_before_cuda(args, fragment):
+    hl.load()
+    d, m, ns, cells, dts = args
+    with pytest.raises((hl.HLError, ValueError)) as ei:
+        if ns == 0:
+            import ctypes
+            lib = hl.load()
+            out = ctypes.c_void_p()
+            rc = lib.hl_create_batch(d, m, 0, None, None, ctypes.byref(out))
+            raise hl.HLError(rc, lib.hl_last_error(None).decode())
+        hl.hl_create_batch(d, m, cells, dts)
+    assert fragment in str(ei.value)
+
+
+def _exact_operator(d, m, lam):
+    """The fused operator in exact rationals (W from the series, H from eq. interp),
+    negated and restricted to the all-lower vertex block, as float64."""
+    from fractions import Fraction as Fr
+    from itertools import product
+    from math import factorial as fac
+    from oracle.hermite import hermite_inverse_exact
+    H = hermite_inverse_exact(m)
+    n, A = m + 1, 2 * m + 2
+    nq = n ** d
+    lamf = [Fr(x) for x in lam]
+    out = np.zeros((d, nq, nq))
+    for i in range(d):
+        for s in range(nq):
+            sv = [(s // n ** k) % n for k in range(d)]
+            for l in range(nq):
+                lv = [(l // n ** k) % n for k in range(d)]
+                acc = Fr(0)
+                for b in product(range(m + 1), repeat=d):
+                    a = [sv[k] + 2 * b[k] + (k == i) for k in range(d)]
+                    if max(a) > 2 * m + 1:
+                        continue
+                    K = sum(b)
+                    w = Fr(2 * fac(K), fac(2 * K + 1))
+                    for k in range(d):
+                        w *= Fr(fac(a[k]), fac(sv[k]) * fac(b[k])) * lamf[k] ** (a[k] - sv[k])
+                        w *= H[a[k]][lv[k]]
+                    acc -= w
+                out[i, l, s] = float(acc)
+    return out
+
+
+@pytest.mark.parametrize("d,m,lam", [(1, 3, [0.45]), (1, 6, [0.3]), (2, 3, [0.45, 0.45]), (2, 2, [0.4, 0.31]),
+                                     (3, 2, [0.45, 0.37, 0.29])])
+def test_operator_table_is_correctly_rounded(d, m, lam):
+    """The library composes its operator in double-double: every entry must equal the
+    exact rational value rounded once (within one ulp)."""
+    got = hl.hl_operator_table(d, m, lam)
+    want = _exact_operator(d, m, lam)
+    ulp = np.spacing(np.abs(want))
+    assert np.all(np.abs(got - want) <= ulp + 1e-300)

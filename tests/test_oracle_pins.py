@@ -444,3 +444,22 @@ def test_source_superposition():
     ps, us = oracle.run_source(d, m, ncell, dt, np.zeros_like(st.p), np.zeros_like(st.u), 12, **args)
     np.testing.assert_allclose(pf, p0 + ps, rtol=0, atol=1e-12 * np.abs(pf).max())
     np.testing.assert_allclose(uf, u0 + us, rtol=0, atol=1e-12 * np.abs(uf).max())
+
+
+def test_long_double_build_agrees_with_binary64():
+    """The long double build (the judge of long GPU runs) is the same algorithm: on a short
+    run the two builds agree to binary64 rounding, and on the 1000-step 1D workload they
+    differ by no more than the binary64 build's accumulated rounding."""
+    d, m, ncell = 2, 3, [12, 10]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=31)
+    p64, u64 = oracle.run(d, m, ncell, dt, st.p, st.u, 3)
+    pld, uld = oracle.run(d, m, ncell, dt, st.p, st.u, 3, prec="ld")
+    assert np.abs(p64 - pld).max() <= 1e-13 * np.abs(pld).max()
+    assert np.abs(u64 - uld).max() <= 1e-13 * np.abs(uld).max()
+    d, m, ncell = 1, 3, [64]
+    dt = I.cfl_dt(ncell)
+    st = I.standing_mode(d, m, ncell, dt, wave=[3])
+    p64, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000)
+    pld, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="ld")
+    assert np.abs(p64 - pld).max() <= 1e-11 * np.abs(pld).max()
