@@ -463,3 +463,59 @@ def test_long_double_build_agrees_with_binary64():
     p64, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000)
     pld, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="ld")
     assert np.abs(p64 - pld).max() <= 1e-11 * np.abs(pld).max()
+
+
+# ----------------------------------------------------------------------------- learned correction
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    params = mlp.init_params(rng, n_in=6, n_h=5, n_out=3)
+    for k in params:
+        params[k] = params[k] + 0.1 * rng.standard_normal(params[k].shape)   # non-zero biases
+    X = rng.standard_normal((7, 6))
+    T = rng.standard_normal((7, 3))
+    _, g = mlp.loss_and_grads(params, X, T)
+    h = 1e-6
+    for k, v in params.items():
+        it = np.nditer(v, flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            old = v[idx]
+            v[idx] = old + h
+            lp, _ = mlp.loss_and_grads(params, X, T)
+            v[idx] = old - h
+            lm, _ = mlp.loss_and_grads(params, X, T)
+            v[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k][idx]) <= 1e-6 * max(1.0, abs(fd)), (k, idx, fd, g[k][idx])
+
+
+def test_restriction_of_fine_analytic_data_is_coarse_analytic_data():
+    """Scaled derivatives restricted from a 4x finer grid equal the coarse grid's own
+    samples of the same analytic field (h^|a| scaling with h_c = 4 h_f)."""
+    from oracle import mlp
+    m = 3
+    nc, r = [20, 16], 4
+    nf = [nc[0] * r, nc[1] * r]
+    fine = I.standing_mode(2, m, nf, 0.01, wave=[2, 1])
+    coarse = I.standing_mode(2, m, nc, 0.01, wave=[2, 1])
+    got = mlp.restrict_p(fine.p, nf, r, m)
+    np.testing.assert_allclose(got, coarse.p, rtol=0, atol=1e-12)
+
+
+def test_features_follow_translation():
+    """Shifting the fields by whole cells shifts the feature rows with them."""
+    from oracle import mlp
+    m, ncell = 3, [10, 8]
+    st = I.random_state(2, m, ncell, seed=2)
+    nq = (m + 1) ** 2
+    P = st.p.reshape(8, 10, nq)
+    U = st.u.reshape(2, 8, 10, nq)
+    Ps = np.roll(P, shift=(2, 3), axis=(0, 1)).reshape(-1, nq)
+    Us = np.roll(U, shift=(2, 3), axis=(1, 2)).reshape(2, -1, nq)
+    nodes = [0, 13, 79]
+    f0 = mlp.features(st.p, st.u, ncell, nodes, 0.5, 0.25)
+    moved = [((n // 10 + 2) % 8) * 10 + (n % 10 + 3) % 10 for n in nodes]
+    f1 = mlp.features(Ps, Us, ncell, moved, 0.5, 0.25)
+    np.testing.assert_array_equal(f0, f1)
+    assert np.all(f0[:, 272] == 0.25) and np.all(f0[:, 273:] == 0.0)
