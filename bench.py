@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hl", "reference"], default="hl")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["2d", "1d", "3d", "batch"], default="2d",
+    ap.add_argument("--workload", choices=["2d", "1d", "3d", "batch", "mixed3d", "mixed2d", "learned"], default="2d",
                     help="2d: the headline line; the others measure further rows of the solver")
     return ap.parse_args()
 
@@ -231,6 +231,69 @@ def run_aux(args):
                     "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                                  "unit": "TFLOP/s", "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS},
                     "status": rc})
+    elif args.workload in ("mixed3d", "mixed2d"):
+        # each precision mode on the same problem: DOF-updates/s beside its L2 error
+        if args.workload == "mixed3d":
+            d, m, ncell, lf = 3, 2, [256, 256, 256], 100
+            dt = I.cfl_dt(ncell)
+            st = I.plane_wave(m, ncell, dt, seed=3)
+            ex = I.plane_wave(m, ncell, dt, seed=3, t0=lf * dt)
+            desc = "3D, 256^3 nodes per grid, m=2, plane wave |n|<=8 (seed 3), 100 steps"
+        else:
+            d, m, ncell, lf = 2, 3, [512, 512], 200
+            dt = I.cfl_dt(ncell)
+            st = I.gaussian_pulse(d, m, ncell, dt, seed=1)
+            ex = None
+            desc = "2D, 512^2 nodes per grid, m=3, Gaussian pulse (seed 1), 200 steps"
+        nnode = int(np.prod(ncell))
+        dof = (d + 1) * (m + 1) ** d * nnode
+        modes = {}
+        ref_p = None
+        for name, mode in (("fp64", hl.HL_FP64), ("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)):
+            h = hl.hl_create(d, m, ncell, dt)
+            hl.hl_set_stream(h, stream)
+            hl.hl_set_precision(h, mode)
+            hl.hl_set_initial(h, st.p, st.u)
+            hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hl.hl_step(h, lf)
+            e1.record(stream)
+            hl.hl_sync(h)
+            ms = e0.elapsed_time(e1)
+            kt, kc = hl.hl_kernel_times(h)
+            pg, ug, _, _ = hl.hl_get_fields(h)
+            hl.hl_destroy(h)
+            r = {"value": dof * lf / (ms / 1e3), "ms_per_step": ms / lf,
+                 "p_half_us": 1e3 * kt["p_half"] / max(kc["p_half"], 1),
+                 "u_half_us": 1e3 * kt["u_half"] / max(kc["u_half"], 1)}
+            if ex is not None:
+                r["l2_err_p_vs_exact"] = I.l2_error(d, ncell, pg, ex.p)
+            if ref_p is None:
+                ref_p = pg
+            else:
+                r["max_rel_diff_vs_fp64"] = float(np.abs(pg - ref_p).max() / np.abs(ref_p).max())
+            # HBM-bound modes: state bytes moved per step / step time vs measured copy bandwidth
+            nq = (m + 1) ** d
+            bytes_step = (3 * d + 3) * nq * 8 * nnode
+            r["hbm_gbs"] = bytes_step / (ms / lf / 1e3) / 1e9
+            modes[name] = r
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        for name in ("fp32", "fp32_comp"):
+            modes[name]["roofline"] = {"bound": "hbm", "achieved": modes[name]["hbm_gbs"], "peak": hbm,
+                                       "unit": "GB/s", "frac": modes[name]["hbm_gbs"] / hbm,
+                                       "peak_source": "measured" if peaks else "fallback"}
+        out.update({"workload": args.workload, "value": modes["fp32_comp"]["value"],
+                    "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
+                    "modes": modes})
+    elif args.workload == "learned":
+        out.update(run_learned(args))
     else:
         d, m, n_shots, lf = 2, 3, 64, 500
         rng = np.random.default_rng(2024)
@@ -264,6 +327,132 @@ def run_aux(args):
                                  "unit": "TFLOP/s", "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS},
                     "status": rc})
     print(json.dumps(out), flush=True)
+
+
+def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
+    """Learned coarse-grid correction at the workload's scale: coarse 256^2 vs fine 1024^2,
+    m = 3, seeded Gaussian pulses and Ricker sources; the fine FP64 solver is the judge."""
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import hl
+    from paper_1808_10481_gb300 import inputs as I
+
+    nc, r = [256, 256], 4
+    nf = [nc[0] * r, nc[1] * r]
+    rows = nc[0] * nc[1]
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+
+    def make(seed, ncell):
+        rng = np.random.default_rng(seed)
+        dt = I.cfl_dt(ncell)
+        h = hl.hl_create(2, 3, ncell, dt)
+        hl.hl_set_stream(h, stream)
+        if seed % 2 == 0:
+            st = I.gaussian_pulse(2, 3, ncell, dt, seed=seed, width=float(rng.uniform(0.012, 0.025)))
+            hl.hl_set_initial(h, st.p, st.u)
+        else:
+            nq = 16
+            hl.hl_set_initial(h, np.zeros((ncell[0] * ncell[1], nq)), np.zeros((2, ncell[0] * ncell[1], nq)))
+            hl.hl_set_source(h, list(rng.random(2)), 0.01, float(rng.uniform(10.0, 20.0)), 1.0)
+        return h
+
+    def pair(seed):
+        hc, hf = make(seed, nc), make(seed, nf)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t2 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        hl.hl_step(hc, horizon)
+        t1.record(stream)
+        hl.hl_step(hf, horizon * r)
+        t2.record(stream)
+        torch.cuda.synchronize()
+        return hc, hf, t0.elapsed_time(t1), t1.elapsed_time(t2)
+
+    gen_rng = np.random.default_rng(0)
+    Xs, Ts, held = [], [], []
+    t_coarse = t_fine = 0.0
+    wall = time.perf_counter()
+    for i in range(n_train + n_test):
+        hc, hf, tc, tf = pair(seed0 + i)
+        t_coarse += tc
+        t_fine += tf
+        if i < n_train:
+            nodes = torch.from_numpy(gen_rng.choice(rows, 16384, replace=False).astype(np.int32)).to(dev)
+            X = torch.empty((16384, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
+            T = torch.empty((16384, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
+            hl.hl_features(hc, nodes, 16384, 1.0, 0.0, X)
+            hl.hl_targets(hf, r, hc, nodes, 16384, 1.0, T)
+            Xs.append(X)
+            Ts.append(T)
+            hl.hl_destroy(hc)
+            hl.hl_destroy(hf)
+        else:
+            T = torch.empty((rows, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
+            hl.hl_targets(hf, r, hc, None, rows, 1.0, T)
+            held.append((hc, hf, T))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - wall
+    X = torch.cat(Xs)
+    T = torch.cat(Ts)
+    out_scale = float(T.pow(2).mean().sqrt())
+    T = T / out_scale
+    n = X.shape[0]
+    net = hl.hl_mlp_create(7)
+    hl.hl_mlp_set_stream(net, stream)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    iters, batch = 3000, 8192
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for it in range(iters):
+        idx = torch.randint(0, n, (batch,), generator=g).to(dev)
+        hl.hl_mlp_loss_grad(net, X[idx].contiguous(), T[idx].contiguous(), batch, want_loss=False)
+        hl.hl_mlp_adam_step(net, 1e-3 if it < 2000 else 2e-4)
+    e1.record(stream)
+    final_loss = hl.hl_mlp_loss_grad(net, X[:65536].contiguous(), T[:65536].contiguous(), min(n, 65536))
+    train_ms = e0.elapsed_time(e1)
+    plain = corr = 0.0
+    plain0 = corr0 = 0.0
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    corr_ms = 0.0
+    for hc, hf, Tt in held:
+        plain += float(Tt.pow(2).sum())
+        plain0 += float(Tt[:, 0].pow(2).sum())
+        e2.record(stream)
+        hl.hl_apply_correction(hc, net, 1.0, 0.0, out_scale)
+        e3.record(stream)
+        T2 = torch.empty_like(Tt)
+        hl.hl_targets(hf, r, hc, None, rows, 1.0, T2)
+        torch.cuda.synchronize()
+        corr_ms += e2.elapsed_time(e3)
+        corr += float(T2.pow(2).sum())
+        corr0 += float(T2[:, 0].pow(2).sum())
+        hl.hl_destroy(hc)
+        hl.hl_destroy(hf)
+    hl.hl_mlp_destroy(net)
+    n_seeds = n_train + n_test
+    dof_c = 3 * 16 * rows * horizon
+    dof_f = 3 * 16 * rows * r * r * horizon * r
+    return {
+        "workload": "learned",
+        "value": dof_c / ((t_coarse / n_seeds + corr_ms / n_test) / 1e3),
+        "config": {"workload": f"learned coarse-grid correction: 2D m=3, coarse 256^2 vs fine 1024^2 (FP64 judge), "
+                               f"{n_train} training + {n_test} held-out seeds (Gaussian pulses width U[0.012,0.025] "
+                               f"and Ricker sources f0 U[10,20]), horizon {horizon} coarse steps",
+                   "mlp": "288-128-128-16, BF16 tensor-core products, FP32 accumulate, Adam",
+                   "train_iters": iters, "batch": batch, "train_rows": n},
+        "held_out_rms_err_plain": (plain / (n_test * rows * 16)) ** 0.5,
+        "held_out_rms_err_corrected": (corr / (n_test * rows * 16)) ** 0.5,
+        "gain_all_slots": (plain / corr) ** 0.5,
+        "gain_value_slot": (plain0 / corr0) ** 0.5,
+        "final_train_loss": final_loss,
+        "ms_coarse_run": t_coarse / n_seeds, "ms_fine_run": t_fine / n_seeds, "ms_correction": corr_ms / n_test,
+        "ms_training": train_ms, "s_data_generation": gen_s,
+        "dof_updates_per_s_coarse_corrected": dof_c / ((t_coarse / n_seeds + corr_ms / n_test) / 1e3),
+        "dof_updates_per_s_fine": dof_f / (t_fine / n_seeds / 1e3),
+    }
 
 
 def main():

@@ -279,6 +279,82 @@ int hl_op_counts(int dim, int m, double *fma_per_node_step, double *add_per_node
  */
 int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
 
+/* ------------------------------------------------------------------------
+ * Learned coarse-grid correction (not in the paper).  A per-node multilayer
+ * perceptron over a coarse 2D m = 3 solution predicts, for every primal node,
+ * corrections to its 16 scaled p values; it is trained on fine-grid solutions
+ * produced by this solver.  Features of coarse primal node J (feat_scale times
+ * the node data, t_feature as given, zero padded):
+ *     p at the 3x3 primal nodes J + {-1,0,1}^2 (y offset outer)      144
+ *     u then v at the cell vertices, dual nodes J + {-1,0}^2          128
+ *     t_feature                                                        1
+ * Network: 288 -> 128 (ReLU) -> 128 (ReLU) -> 16, every product on the tensor
+ * cores with BF16 operands and FP32 accumulation, FP32 master weights and Adam
+ * moments.  Loss: mean of (y - target)^2 over rows and outputs.  Parameter
+ * block (floats): W1[288][128], b1[128], W2[128][128], b2[128], W3[128][16],
+ * b3[16].
+ * Every hl_mlp call runs on the handle's stream (hl_mlp_set_stream); device
+ * buffers are row-major float, one row per node.
+ */
+#define HL_MLP_IN 288
+#define HL_MLP_HIDDEN 128
+#define HL_MLP_OUT 16
+#define HL_MLP_NPARAMS 55568
+
+typedef struct hl_mlp hl_mlp;
+
+/* hl_mlp_create -- allocate a network with He-initialised weights (seeded). */
+int hl_mlp_create(uint64_t seed, hl_mlp **out);
+void hl_mlp_destroy(hl_mlp *mlp);
+const char *hl_mlp_last_error(const hl_mlp *mlp);
+int hl_mlp_set_stream(hl_mlp *mlp, void *cuda_stream);
+
+/*
+ * hl_mlp_params -- host copies of the parameters: get_params/get_grads
+ * receive HL_MLP_NPARAMS floats (the gradients of the last hl_mlp_loss_grad);
+ * set_params replaces the weights and resets Adam.  Any pointer may be NULL.
+ * Synchronises the handle's stream.
+ */
+int hl_mlp_params(hl_mlp *mlp, float *get_params, const float *set_params, float *get_grads);
+
+/* hl_mlp_forward -- Y_dev[rows][16] = network(X_dev[rows][288]). */
+int hl_mlp_forward(hl_mlp *mlp, const float *X_dev, int rows, float *Y_dev);
+
+/*
+ * hl_mlp_loss_grad -- forward, loss against T_dev[rows][16] and the full
+ * gradient (overwrites the previous one).  loss (host, may be NULL) receives
+ * the mean squared error; passing it synchronises the stream.
+ */
+int hl_mlp_loss_grad(hl_mlp *mlp, const float *X_dev, const float *T_dev, int rows, double *loss);
+
+/* hl_mlp_adam_step -- one Adam update (beta1 0.9, beta2 0.999, eps 1e-8) with the current gradient. */
+int hl_mlp_adam_step(hl_mlp *mlp, float lr);
+
+/*
+ * hl_features -- X_dev[rows][288] for the coarse primal nodes nodes_dev[rows]
+ * (device int array; NULL = nodes 0..rows-1) of a single 2D m = 3 grid, on the
+ * solver's stream.  Nodes outside the grid give zero rows.
+ */
+int hl_features(const hl_solver *coarse, const int *nodes_dev, int rows, float feat_scale, float t_feature,
+                float *X_dev);
+
+/*
+ * hl_targets -- T_dev[rows][16] = (fine p restricted to the coarse node -
+ * coarse p) / out_scale.  The fine grid has ratio times the coarse nodes per
+ * axis; coarse primal node J is fine primal node ratio*J and slot a of the
+ * fine data is scaled by ratio^|a| (h^|a| in the scaled derivatives).  Both
+ * solvers must hold data at the same time.  On the coarse solver's stream.
+ */
+int hl_targets(const hl_solver *fine, int ratio, const hl_solver *coarse, const int *nodes_dev, int rows,
+               double out_scale, float *T_dev);
+
+/*
+ * hl_apply_correction -- p~(J) += out_scale * network(features(J)) at every
+ * primal node of the coarse solver (the addition in FP64).  Uses workspace
+ * owned by the network handle.
+ */
+int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_scale, float t_feature, double out_scale);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,12 +9,12 @@ leapfrog subtraction), written in C (``hl_oracle.c``) with the exact-rational
 operator H from ``hermite.py``.
 
 Two builds of the same source: ``prec="f64"`` (IEEE binary64, the paper's
-precision and the timed CPU baseline) and ``prec="ld"`` (long double: x87
-80-bit on x86-64, binary128 on aarch64).  Long runs are judged against the
-``ld`` build, because the binary64 build's own accumulated rounding after
-hundreds of steps (about 1e-12 to 5e-12 relative on the 1D and 2D workloads)
-is as large as the parity bar.  Arrays passed to an ``ld`` call are converted
-to long double; results come back as float64 unless ``raw=True``.
+precision and the timed CPU baseline) and ``prec="dd"`` (double-double, about
+106 significant bits, ``dd.hpp``; the same bits on every platform).  Long runs
+are judged against the ``dd`` build, because the binary64 build's own
+accumulated rounding after hundreds of steps (about 1e-12 to 5e-12 relative on
+the 1D and 2D workloads) is as large as the parity bar.  Arrays passed to a
+``dd`` call become (hi, lo = 0) pairs; results come back rounded to float64.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against facts the
 paper and the mathematics fix (polynomial reproduction, exact local evolution
@@ -34,27 +34,36 @@ from .hermite import hermite_inverse, hermite_inverse_exact, interp_system
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hl_oracle.c")
 _LIBS = {"f64": os.path.join(_HERE, "_build", "liboracle.so"),
-         "ld": os.path.join(_HERE, "_build", "liboracle_ld.so")}
+         "dd": os.path.join(_HERE, "_build", "liboracle_dd.so")}
+_DEPS = [_SRC, os.path.join(_HERE, "dd.hpp")]
+
+
+class DD(ctypes.Structure):
+    """A double-double scalar as the judge build passes it by value."""
+    _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double)]
 _libs: dict = {}
 
 
 def build(force: bool = False) -> str:
-    """Compile both builds of the C oracle with gcc (OpenMP)."""
+    """Compile both builds of the oracle (gcc, OpenMP): binary64 as C, double-double as C++."""
     for prec, path in _LIBS.items():
         os.makedirs(os.path.dirname(path), exist_ok=True)
-        if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        newest = max(os.path.getmtime(f) for f in _DEPS)
+        if not force and os.path.exists(path) and os.path.getmtime(path) >= newest:
             continue
         tmp = path + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
-        if prec == "ld":
-            cmd.insert(1, "-DORC_LONG")
+        if prec == "dd":
+            cmd = ["g++", "-O2", "-std=c++17", "-x", "c++", "-DORC_DD", "-I" + _HERE, "-ffp-contract=off",
+                   "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        else:
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, path)
     return _LIBS["f64"]
 
 
 def _dtype(prec: str):
-    return np.float64 if prec == "f64" else np.longdouble
+    return np.float64
 
 
 def _load(prec: str = "f64"):
@@ -64,7 +73,7 @@ def _load(prec: str = "f64"):
         raise ValueError("prec must be 'f64' or 'ld'")
     build()
     lib = ctypes.CDLL(_LIBS[prec])
-    R = ctypes.c_double if prec == "f64" else ctypes.c_longdouble
+    R = ctypes.c_double if prec == "f64" else DD
     rp = ctypes.POINTER(R)
     i64p = ctypes.POINTER(ctypes.c_int64)
     I, L = ctypes.c_int, ctypes.c_int64
@@ -87,19 +96,31 @@ def _load(prec: str = "f64"):
 
 
 def _ptr(a: np.ndarray):
-    ct = ctypes.c_double if a.dtype == np.float64 else ctypes.c_longdouble
+    """Pointer to a float64 array (binary64) or to a (..., 2) hi/lo array (double-double)."""
+    ct = DD if (a.ndim and a.shape[-1] == 2 and getattr(a, "_is_dd", False)) else ctypes.c_double
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+class _DDArray(np.ndarray):
+    _is_dd = True
+
+
 def _arr(a, prec: str, copy: bool = False) -> np.ndarray:
-    if copy:
-        return np.array(a, dtype=_dtype(prec), order="C", copy=True)
-    return np.ascontiguousarray(a, dtype=_dtype(prec))
+    x = np.array(a, dtype=np.float64, order="C", copy=True) if copy else np.ascontiguousarray(a, dtype=np.float64)
+    if prec == "f64":
+        return x
+    y = np.zeros(x.shape + (2,), dtype=np.float64)
+    y[..., 0] = x
+    return y.view(_DDArray)
+
+
+def _scalar(x: float, prec: str):
+    return float(x) if prec == "f64" else DD(float(x), 0.0)
 
 
 def _h_array(m: int, prec: str = "f64") -> np.ndarray:
-    # H is dyadic (exact in binary64) for every m <= 6, so both conversions are exact
-    return np.ascontiguousarray(np.array(hermite_inverse(m), dtype=np.float64).astype(_dtype(prec)))
+    # H is dyadic (exact in binary64) for every m <= 6, so the conversion is exact
+    return _arr(np.array(hermite_inverse(m), dtype=np.float64), prec)
 
 
 def _nc(ncell):
@@ -110,14 +131,18 @@ def _i64p(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
-def _out(a: np.ndarray, raw: bool):
-    return a if raw else a.astype(np.float64)
+def _out(a: np.ndarray, raw: bool = False):
+    """float64 result; for a double-double array hi + lo (rounded once), or the pair if raw."""
+    if a.ndim and getattr(a, "_is_dd", False):
+        a = np.asarray(a)
+        return a if raw else a[..., 0] + a[..., 1]
+    return a
 
 
 def lambdas(ncell, dt: float, prec: str = "f64") -> np.ndarray:
     """lam_k = dt / (2 h_k) with h_k = 1/ncell_k (periodic unit box), computed in binary64."""
     lam = np.array([dt * n / 2.0 for n in ncell] + [0.0] * (3 - len(ncell)), dtype=np.float64)
-    return lam.astype(_dtype(prec))
+    return _arr(lam, prec)
 
 
 def set_threads(n: int) -> None:
@@ -138,12 +163,12 @@ def node_update(d: int, m: int, lam, mode: int, vtx: np.ndarray, prec: str = "f6
     lib = _load(prec)
     nq = (m + 1) ** d
     ncs, ncd = (d, 1) if mode == 0 else (1, d)
-    vtx = _arr(vtx, prec).reshape(ncs, 1 << d, nq)
-    out = np.zeros((ncd, nq), dtype=_dtype(prec))
-    lam3 = np.zeros(3, dtype=_dtype(prec))
+    vtx = _arr(np.asarray(vtx, dtype=np.float64).reshape(ncs, 1 << d, nq), prec)
+    out = _arr(np.zeros((ncd, nq)), prec)
+    lam3 = np.zeros(3)
     lam3[:d] = np.asarray(lam, dtype=np.float64)[:d]
-    lib.oracle_node_update(d, m, _ptr(lam3), _ptr(_h_array(m, prec)), mode, _ptr(vtx), _ptr(out))
-    return _out(out, False)
+    lib.oracle_node_update(d, m, _ptr(_arr(lam3, prec)), _ptr(_h_array(m, prec)), mode, _ptr(vtx), _ptr(out))
+    return _out(out)
 
 
 def half_step(d: int, m: int, ncell, dt: float, mode: int, src: np.ndarray, dst: np.ndarray) -> None:
@@ -166,10 +191,10 @@ def half_step_nodes(d: int, m: int, ncell, dt: float, mode: int, src: np.ndarray
     nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
     src = _arr(src, prec)
     dst = _arr(dst, prec)
-    out = np.empty((ncd, nodes.size, nq), dtype=_dtype(prec))
+    out = _arr(np.empty((ncd, nodes.size, nq)), prec)
     lib.oracle_half_step_nodes(d, m, _i64p(_nc(ncell)), _ptr(lambdas(ncell, dt, prec)), _ptr(_h_array(m, prec)),
                                mode, _ptr(src), _ptr(dst), _i64p(nodes), nodes.size, _ptr(out))
-    return _out(out, False)
+    return _out(out)
 
 
 def run(d: int, m: int, ncell, dt: float, p: np.ndarray, u: np.ndarray, n_steps: int, prec: str = "f64",
@@ -203,11 +228,12 @@ def run_source(d: int, m: int, ncell, dt: float, p, u, n_steps: int, x0, sigma: 
     lib = _load(prec)
     p = _arr(p, prec, copy=True)
     u = _arr(u, prec, copy=True)
-    x = np.zeros(3, dtype=_dtype(prec))
+    x = np.zeros(3)
     x[:d] = np.asarray(x0, dtype=np.float64)[:d]
+    x = _arr(x, prec)
     lib.oracle_run_source(d, m, _i64p(_nc(ncell)), _ptr(lambdas(ncell, dt, prec)), _ptr(_h_array(m, prec)),
-                          float(dt), _ptr(x), float(sigma), float(f0), float(amp), int(step0), _ptr(p), _ptr(u),
-                          int(n_steps))
+                          _scalar(dt, prec), _ptr(x), _scalar(sigma, prec), _scalar(f0, prec), _scalar(amp, prec),
+                          int(step0), _ptr(p), _ptr(u), int(n_steps))
     return _out(p, raw), _out(u, raw)
 
 

@@ -47,16 +47,18 @@
 #include <omp.h>
 #endif
 
-/* The source is precision-generic.  The default build uses IEEE binary64
- * (the paper's precision, Section 6).  Built with -DORC_LONG it uses long
- * double (x87 80-bit on x86-64, binary128 on aarch64): the same steps with a
- * smaller rounding error, used to judge long runs against a 1e-12 bar that
- * lies below the binary64 build's own accumulated rounding. */
-#ifdef ORC_LONG
-typedef long double orc_real;
-#define ORC_POW powl
-#define ORC_EXP expl
-#define ORC_FLOOR floorl
+/* The source is precision-generic.  The default build (C) uses IEEE
+ * binary64, the paper's precision (Section 6).  Built as C++ with -DORC_DD it
+ * uses double-double arithmetic (dd.hpp, about 106 significant bits): the same
+ * steps with a far smaller rounding error, used to judge long runs against a
+ * 1e-12 bar that lies below the binary64 build's own accumulated rounding. */
+#ifdef ORC_DD
+#include "dd.hpp"
+typedef orc_dd orc_real;
+#define ORC_POW orc_dd_pow
+#define ORC_EXP orc_dd_exp
+#define ORC_FLOOR orc_dd_floor
+extern "C" {
 #else
 typedef double orc_real;
 #define ORC_POW pow
@@ -308,8 +310,8 @@ void oracle_run(int d, int m, const int64_t *ncell, const orc_real *lam, const o
  * forced experiments add a source z(x,t) to the pressure equation (Section 4,
  * eq. waveEq1D) without stating its time discretisation; here the source
  *     f(x,t) = amp * R(t) * g(x),
- *     R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) ORC_EXP(-pi^2 f0^2 (t-t0)^2),  t0 = 1.2/f0,
- *     g(x) = ORC_EXP(-|x - x0|^2 / (2 sigma^2))   (nearest periodic image),
+ *     R(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2),  t0 = 1.2/f0,
+ *     g(x) = exp(-|x - x0|^2 / (2 sigma^2))   (nearest periodic image),
  * enters the p-half by the midpoint rule: p~_a += dt * amp * R(t_n + dt/2) * g~_a,
  * with g~_a the exact scaled derivatives prod_k h_k^{a_k}/a_k! d^{a_k} g_k. */
 static orc_real orc_ricker(orc_real t, orc_real f0)
@@ -320,8 +322,8 @@ static orc_real orc_ricker(orc_real t, orc_real f0)
     return (1.0 - 2.0 * arg) * ORC_EXP(-arg);
 }
 
-/* scaled derivatives (h^a/a!) d^a/dx^a ORC_EXP(-z^2/2), z = (x - c)/sigma, a = 0..m:
- * d^a ORC_EXP(-z^2/2)/dx^a = (-1/sigma)^a He_a(z) ORC_EXP(-z^2/2) (probabilists' Hermite). */
+/* scaled derivatives (h^a/a!) d^a/dx^a exp(-z^2/2), z = (x - c)/sigma, a = 0..m:
+ * d^a exp(-z^2/2)/dx^a = (-1/sigma)^a He_a(z) exp(-z^2/2) (probabilists' Hermite). */
 static void orc_gauss_1d(orc_real dx, orc_real sigma, orc_real h, int m, orc_real *out)
 {
     const orc_real z = dx / sigma;
@@ -398,3 +400,7 @@ int oracle_threads(void)
     return 1;
 #endif
 }
+
+#ifdef ORC_DD
+}  /* extern "C" */
+#endif

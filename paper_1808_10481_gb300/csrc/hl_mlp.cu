@@ -1,0 +1,566 @@
+// Learned coarse-grid correction (not in the paper): a per-node MLP over the
+// coarse solver's Hermite data, trained on fine-grid solutions.
+//
+//   features of coarse primal node J (2D, m = 3, nq = 16), all times feat_scale
+//   except the time feature:
+//     p at the 3x3 primal nodes J + {-1,0,1}^2 (dy outer, dx inner)     144
+//     u, then v, at the cell vertices: dual nodes J + {-1,0}^2             128
+//     t_feature                                                              1
+//     zero padding                                                          15  -> 288
+//   y = relu(relu(x W1 + b1) W2 + b2) W3 + b3            288 -> 128 -> 128 -> 16
+//   p~(J) += out_scale * y   (added in FP64)
+//
+// Every matrix product runs on the tensor cores through a warp-level
+// mma.sync m16n8k16 with BF16 operands (weights and activations rounded to
+// BF16 when staged) and FP32 accumulation; master weights, Adam moments and
+// activations are FP32.  Loss: mean over rows and outputs of (y - target)^2.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/hl.h"
+#include "hl_internal.h"
+#include "hl_solver.h"
+
+namespace hl {
+
+constexpr int kIn = HL_MLP_IN, kH = HL_MLP_HIDDEN, kOut = HL_MLP_OUT;
+
+// ---------------------------------------------------------------------------
+// C[M x N] = A[M x K] B[K x N] (+ bias[n]) (relu) ; element (r, c) of a matrix X
+// is X.p[r * X.rs + c * X.cs], so transposes are free.  64x64 block tile,
+// 4 warps of 32x32, K staged 32 at a time through shared memory as BF16.
+struct Mat {
+    const float *p;
+    int64_t rs, cs;
+};
+
+constexpr int BM = 64, BN = 64, BK = 32;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ C, int64_t ldc, int M, int N, int K,
+                                              const float *__restrict__ bias, int relu)
+{
+    __shared__ float As[BM][BK + 1];
+    __shared__ float Bs[BK][BN + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 128) {
+            const int r = e / BK, c = e % BK;
+            const int gr = m0 + r, gc = k0 + c;
+            As[r][c] = (gr < M && gc < K) ? A.p[(int64_t)gr * A.rs + (int64_t)gc * A.cs] : 0.f;
+        }
+        for (int e = tid; e < BK * BN; e += 128) {
+            const int r = e / BN, c = e % BN;
+            const int gr = k0 + r, gc = n0 + c;
+            Bs[r][c] = (gr < K && gc < N) ? B.p[(int64_t)gr * B.rs + (int64_t)gc * B.cs] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + g;
+                af[i][0] = pack_bf16(As[r][kk + 2 * t], As[r][kk + 2 * t + 1]);
+                af[i][1] = pack_bf16(As[r + 8][kk + 2 * t], As[r + 8][kk + 2 * t + 1]);
+                af[i][2] = pack_bf16(As[r][kk + 2 * t + 8], As[r][kk + 2 * t + 9]);
+                af[i][3] = pack_bf16(As[r + 8][kk + 2 * t + 8], As[r + 8][kk + 2 * t + 9]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + g;
+                bf[j][0] = pack_bf16(Bs[kk + 2 * t][c], Bs[kk + 2 * t + 1][c]);
+                bf[j][1] = pack_bf16(Bs[kk + 2 * t + 8][c], Bs[kk + 2 * t + 9][c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+                        : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = m0 + wm + i * 16 + g + (e >= 2 ? 8 : 0);
+                const int c = n0 + wn + j * 8 + 2 * t + (e & 1);
+                if (r < M && c < N) {
+                    float v = acc[i][j][e];
+                    if (bias) v += bias[c];
+                    if (relu) v = fmaxf(v, 0.f);
+                    C[(int64_t)r * ldc + c] = v;
+                }
+            }
+}
+
+static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K, const float *bias, int relu,
+                        cudaStream_t st)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+    k_gemm<<<grid, 128, 0, st>>>(A, B, C, ldc, M, N, K, bias, relu);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// elementwise and reduction kernels
+__global__ void k_mse(const float *__restrict__ Y, const float *__restrict__ T, float *__restrict__ dY, int64_t n,
+                      double *loss)
+{
+    double local = 0.0;
+    const double inv = 1.0 / (double)n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float r = Y[e] - T[e];
+        dY[e] = (float)(2.0 * r * inv);
+        local += (double)r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, local * inv);
+}
+
+// dH *= (H > 0): the ReLU derivative taken from the post-activation value
+__global__ void k_relu_mask(float *__restrict__ dH, const float *__restrict__ H, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        if (!(H[e] > 0.f)) dH[e] = 0.f;
+}
+
+// db[c] = sum_r dX[r][c]
+__global__ void k_colsum(const float *__restrict__ dX, float *__restrict__ db, int rows, int cols)
+{
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += dX[(int64_t)r * cols + c];
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] = red[0];
+}
+
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
+                       float *__restrict__ m2, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[e];
+        const float a = b1 * m1[e] + (1.f - b1) * gi;
+        const float b = b2 * m2[e] + (1.f - b2) * gi * gi;
+        m1[e] = a;
+        m2[e] = b;
+        w[e] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+    }
+}
+
+// features of the listed coarse primal nodes (2D, m = 3), slot-major state
+__global__ void k_features(const double *__restrict__ P, const double *__restrict__ U, int n0, int n1,
+                           int64_t nnode, const int *__restrict__ nodes, int rows, float feat_scale, float t_feature,
+                           float *__restrict__ X)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * kIn) return;
+    const int r = (int)(e / kIn), col = (int)(e % kIn);
+    const int node = nodes ? nodes[r] : r;
+    float v = 0.f;
+    if (node < 0 || node >= nnode) {  // a bad caller-supplied node reads nothing
+        X[e] = 0.f;
+        return;
+    }
+    const int jx = node % n0, jy = node / n0;
+    if (col < 144) {
+        const int blk = col / 16, q = col % 16;
+        const int dy = blk / 3 - 1, dx = blk % 3 - 1;
+        const int x = (jx + dx + n0) % n0, y = (jy + dy + n1) % n1;
+        v = feat_scale * (float)P[(int64_t)q * nnode + x + (int64_t)n0 * y];
+    } else if (col < 272) {
+        const int c2 = col - 144;
+        const int comp = c2 / 64, blk = (c2 % 64) / 16, q = c2 % 16;
+        const int vy = blk / 2 - 1, vx = blk % 2 - 1;
+        const int x = (jx + vx + n0) % n0, y = (jy + vy + n1) % n1;
+        v = feat_scale * (float)U[(int64_t)(comp * 16 + q) * nnode + x + (int64_t)n0 * y];
+    } else if (col == 272) {
+        v = t_feature;
+    }
+    X[e] = v;
+}
+
+// targets (restricted fine p - coarse p) / out_scale at the listed coarse nodes
+__global__ void k_targets(const double *__restrict__ Pf, int nf0, int64_t nnode_f, int ratio,
+                          const double *__restrict__ Pc, int nc0, int64_t nnode_c, const int *__restrict__ nodes,
+                          int rows, double inv_scale, float *__restrict__ T)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * kOut) return;
+    const int r = (int)(e / kOut), q = (int)(e % kOut);
+    const int node = nodes ? nodes[r] : r;
+    if (node < 0 || node >= nnode_c) {  // a bad caller-supplied node reads nothing
+        T[e] = 0.f;
+        return;
+    }
+    const int jx = node % nc0, jy = node / nc0;
+    const int a = (q % 4) + (q / 4);
+    double scale = 1.0;
+    for (int k = 0; k < a; ++k) scale *= ratio;
+    const double fine = Pf[(int64_t)q * nnode_f + (int64_t)jx * ratio + (int64_t)nf0 * ((int64_t)jy * ratio)];
+    T[e] = (float)((fine * scale - Pc[(int64_t)q * nnode_c + node]) * inv_scale);
+}
+
+__global__ void k_correct(double *__restrict__ P, int64_t nnode, const float *__restrict__ Y, int rows,
+                          double out_scale)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * kOut) return;
+    const int r = (int)(e / kOut), q = (int)(e % kOut);
+    P[(int64_t)q * nnode + r] += out_scale * (double)Y[e];
+}
+
+static unsigned blocks_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace hl
+
+using namespace hl;
+
+// parameter block layout (floats): W1 [kIn][kH], b1 [kH], W2 [kH][kH], b2 [kH], W3 [kH][kOut], b3 [kOut]
+static constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (int64_t)kIn * kH, OFF_W2 = OFF_B1 + kH,
+                         OFF_B2 = OFF_W2 + (int64_t)kH * kH, OFF_W3 = OFF_B2 + kH, OFF_B3 = OFF_W3 + (int64_t)kH * kOut,
+                         N_PARAMS = OFF_B3 + kOut;
+static_assert(N_PARAMS == HL_MLP_NPARAMS, "parameter count and header disagree");
+
+struct hl_mlp {
+    float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // N_PARAMS each
+    float *work = nullptr;   // per-row activations: H1, H2, Y, dY, dH2, dH1
+    int64_t rows_cap = 0;
+    double *loss = nullptr;  // device
+    double *loss_host = nullptr;
+    int64_t adam_t = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool poisoned = false;
+};
+
+static thread_local std::string g_mlp_error;
+
+static int mlp_err(hl_mlp *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg; else g_mlp_error = msg;
+    return code;
+}
+
+static int mlp_cuda(hl_mlp *h, cudaError_t e, const char *what)
+{
+    if (h) h->poisoned = true;
+    return mlp_err(h, HL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MLP_CK(h, call)                                        \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return mlp_cuda(h, e_, #call);  \
+    } while (0)
+
+static int mlp_check(hl_mlp *h)
+{
+    if (!h) return mlp_err(nullptr, HL_EINVAL, "null mlp handle");
+    if (h->poisoned) return mlp_err(h, HL_ESTATE, "mlp handle poisoned: " + h->err);
+    return HL_OK;
+}
+
+// rows x (H1, H2, Y, dY, dH2, dH1)
+static int ensure_rows(hl_mlp *h, int64_t rows)
+{
+    if (rows <= h->rows_cap) return HL_OK;
+    if (h->work) {
+        MLP_CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->work);
+        h->work = nullptr;
+    }
+    const int64_t per = 2 * kH + 2 * kOut + 2 * kH;
+    cudaError_t e = cudaMalloc(&h->work, (size_t)rows * per * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->rows_cap = 0;
+        return mlp_err(h, HL_ENOMEM, "mlp workspace allocation failed");
+    }
+    h->rows_cap = rows;
+    return HL_OK;
+}
+
+struct Work {
+    float *H1, *H2, *Y, *dY, *dH2, *dH1;
+};
+
+static Work work_ptrs(hl_mlp *h, int64_t rows)
+{
+    Work w;
+    w.H1 = h->work;
+    w.H2 = w.H1 + rows * kH;
+    w.Y = w.H2 + rows * kH;
+    w.dY = w.Y + rows * kOut;
+    w.dH2 = w.dY + rows * kOut;
+    w.dH1 = w.dH2 + rows * kH;
+    return w;
+}
+
+static cudaError_t forward_into(hl_mlp *h, const float *X, int rows, const Work &w, float *Y)
+{
+    cudaError_t e;
+    if ((e = gemm({X, kIn, 1}, {h->w + OFF_W1, kH, 1}, w.H1, kH, rows, kH, kIn, h->w + OFF_B1, 1, h->stream)) != cudaSuccess)
+        return e;
+    if ((e = gemm({w.H1, kH, 1}, {h->w + OFF_W2, kH, 1}, w.H2, kH, rows, kH, kH, h->w + OFF_B2, 1, h->stream)) != cudaSuccess)
+        return e;
+    return gemm({w.H2, kH, 1}, {h->w + OFF_W3, kOut, 1}, Y, kOut, rows, kOut, kH, h->w + OFF_B3, 0, h->stream);
+}
+
+extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
+{
+    if (!out) return mlp_err(nullptr, HL_EINVAL, "out is NULL");
+    *out = nullptr;
+    hl_mlp *h = new hl_mlp();
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->w, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->g, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m1, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->m2, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->loss, sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost(&h->loss_host, sizeof(double))) != cudaSuccess) {
+        std::string msg = std::string("mlp set-up failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        hl_mlp_destroy(h);
+        return mlp_err(nullptr, e == cudaErrorMemoryAllocation ? HL_ENOMEM : HL_ECUDA, msg);
+    }
+    // He initialisation (normal, std sqrt(2/fan_in); last layer sqrt(1/fan_in)), zero biases
+    std::vector<float> w(N_PARAMS, 0.f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int64_t i = 0; i < (int64_t)kIn * kH; ++i) w[OFF_W1 + i] = nd(rng) * std::sqrt(2.f / kIn);
+    for (int64_t i = 0; i < (int64_t)kH * kH; ++i) w[OFF_W2 + i] = nd(rng) * std::sqrt(2.f / kH);
+    for (int64_t i = 0; i < (int64_t)kH * kOut; ++i) w[OFF_W3 + i] = nd(rng) * std::sqrt(1.f / kH);
+    if ((e = cudaMemcpy(h->w, w.data(), N_PARAMS * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->g, 0, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(h->m1, 0, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(h->m2, 0, N_PARAMS * sizeof(float))) != cudaSuccess) {
+        std::string msg = std::string("mlp set-up failed: ") + cudaGetErrorString(e);
+        hl_mlp_destroy(h);
+        return mlp_err(nullptr, HL_ECUDA, msg);
+    }
+    *out = h;
+    return HL_OK;
+}
+
+extern "C" void hl_mlp_destroy(hl_mlp *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    cudaFree(h->w);
+    cudaFree(h->g);
+    cudaFree(h->m1);
+    cudaFree(h->m2);
+    cudaFree(h->work);
+    cudaFree(h->loss);
+    if (h->loss_host) cudaFreeHost(h->loss_host);
+    delete h;
+}
+
+extern "C" const char *hl_mlp_last_error(const hl_mlp *h) { return h ? h->err.c_str() : g_mlp_error.c_str(); }
+
+extern "C" int hl_mlp_set_stream(hl_mlp *h, void *cuda_stream)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    MLP_CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = (cudaStream_t)cuda_stream;
+    return HL_OK;
+}
+
+extern "C" int hl_mlp_params(hl_mlp *h, float *get_params, const float *set_params, float *get_grads)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    MLP_CK(h, cudaStreamSynchronize(h->stream));
+    if (set_params) {
+        MLP_CK(h, cudaMemcpy(h->w, set_params, N_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+        MLP_CK(h, cudaMemset(h->m1, 0, N_PARAMS * sizeof(float)));
+        MLP_CK(h, cudaMemset(h->m2, 0, N_PARAMS * sizeof(float)));
+        h->adam_t = 0;
+    }
+    if (get_params) MLP_CK(h, cudaMemcpy(get_params, h->w, N_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+    if (get_grads) MLP_CK(h, cudaMemcpy(get_grads, h->g, N_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+    return HL_OK;
+}
+
+extern "C" int hl_mlp_forward(hl_mlp *h, const float *X_dev, int rows, float *Y_dev)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    if (rows < 0 || (!X_dev && rows) || (!Y_dev && rows)) return mlp_err(h, HL_EINVAL, "bad forward arguments");
+    if (rows == 0) return HL_OK;
+    rc = ensure_rows(h, rows);
+    if (rc) return rc;
+    MLP_CK(h, forward_into(h, X_dev, rows, work_ptrs(h, rows), Y_dev));
+    return HL_OK;
+}
+
+extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_dev, int rows, double *loss)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    if (rows <= 0 || !X_dev || !T_dev) return mlp_err(h, HL_EINVAL, "bad loss_grad arguments");
+    rc = ensure_rows(h, rows);
+    if (rc) return rc;
+    const Work w = work_ptrs(h, rows);
+    const cudaStream_t st = h->stream;
+    MLP_CK(h, forward_into(h, X_dev, rows, w, w.Y));
+    MLP_CK(h, cudaMemsetAsync(h->loss, 0, sizeof(double), st));
+    const int64_t ny = (int64_t)rows * kOut;
+    k_mse<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, T_dev, w.dY, ny, h->loss);
+    MLP_CK(h, cudaGetLastError());
+    // layer 3
+    MLP_CK(h, gemm({w.H2, 1, kH}, {w.dY, kOut, 1}, h->g + OFF_W3, kOut, kH, kOut, rows, nullptr, 0, st));
+    k_colsum<<<kOut, 256, 0, st>>>(w.dY, h->g + OFF_B3, rows, kOut);
+    MLP_CK(h, gemm({w.dY, kOut, 1}, {h->w + OFF_W3, 1, kOut}, w.dH2, kH, rows, kH, kOut, nullptr, 0, st));
+    k_relu_mask<<<blocks_for((int64_t)rows * kH, 256), 256, 0, st>>>(w.dH2, w.H2, (int64_t)rows * kH);
+    // layer 2
+    MLP_CK(h, gemm({w.H1, 1, kH}, {w.dH2, kH, 1}, h->g + OFF_W2, kH, kH, kH, rows, nullptr, 0, st));
+    k_colsum<<<kH, 256, 0, st>>>(w.dH2, h->g + OFF_B2, rows, kH);
+    MLP_CK(h, gemm({w.dH2, kH, 1}, {h->w + OFF_W2, 1, kH}, w.dH1, kH, rows, kH, kH, nullptr, 0, st));
+    k_relu_mask<<<blocks_for((int64_t)rows * kH, 256), 256, 0, st>>>(w.dH1, w.H1, (int64_t)rows * kH);
+    // layer 1
+    MLP_CK(h, gemm({X_dev, 1, kIn}, {w.dH1, kH, 1}, h->g + OFF_W1, kH, kIn, kH, rows, nullptr, 0, st));
+    k_colsum<<<kH, 256, 0, st>>>(w.dH1, h->g + OFF_B1, rows, kH);
+    MLP_CK(h, cudaGetLastError());
+    if (loss) {
+        MLP_CK(h, cudaMemcpyAsync(h->loss_host, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MLP_CK(h, cudaStreamSynchronize(st));
+        *loss = *h->loss_host;
+    }
+    return HL_OK;
+}
+
+extern "C" int hl_mlp_adam_step(hl_mlp *h, float lr)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_err(h, HL_EINVAL, "lr must be finite and > 0");
+    h->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)h->adam_t), c2 = 1.f - std::pow(b2, (float)h->adam_t);
+    k_adam<<<blocks_for(N_PARAMS, 256), 256, 0, h->stream>>>(h->w, h->g, h->m1, h->m2, N_PARAMS, lr, b1, b2, 1e-8f,
+                                                            c1, c2);
+    MLP_CK(h, cudaGetLastError());
+    return HL_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int solver_ok(const hl_solver *s)
+{
+    if (!s) return mlp_err(nullptr, HL_EINVAL, "null solver handle");
+    if (s->poisoned) return mlp_err(nullptr, HL_ESTATE, "solver handle poisoned");
+    if (s->dim != 2 || s->m != 3 || s->shots.size() != 1)
+        return mlp_err(nullptr, HL_EINVAL, "the learned correction needs a single 2D m = 3 grid");
+    return HL_OK;
+}
+
+extern "C" int hl_features(const hl_solver *coarse, const int *nodes_dev, int rows, float feat_scale,
+                           float t_feature, float *X_dev)
+{
+    int rc = solver_ok(coarse);
+    if (rc) return rc;
+    if (rows < 0 || (rows && !X_dev)) return mlp_err(nullptr, HL_EINVAL, "bad feature arguments");
+    if (!nodes_dev && rows > coarse->shots[0].nnode) return mlp_err(nullptr, HL_EINVAL, "rows exceed the grid");
+    if (rows == 0) return HL_OK;
+    const Shot &s = coarse->shots[0];
+    const int64_t n = (int64_t)rows * kIn;
+    k_features<<<(unsigned)((n + 255) / 256), 256, 0, coarse->stream>>>(
+        coarse->p, coarse->u, (int)s.n[0], (int)s.n[1], s.nnode, nodes_dev, rows, feat_scale, t_feature, X_dev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HL_OK : mlp_err(nullptr, HL_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int hl_targets(const hl_solver *fine, int ratio, const hl_solver *coarse, const int *nodes_dev, int rows,
+                          double out_scale, float *T_dev)
+{
+    int rc = solver_ok(fine);
+    if (rc) return rc;
+    rc = solver_ok(coarse);
+    if (rc) return rc;
+    const Shot &f = fine->shots[0], &c = coarse->shots[0];
+    if (ratio < 1 || f.n[0] != c.n[0] * ratio || f.n[1] != c.n[1] * ratio)
+        return mlp_err(nullptr, HL_EINVAL, "fine grid must be ratio times the coarse grid");
+    if (rows < 0 || (rows && !T_dev) || !(out_scale > 0.0)) return mlp_err(nullptr, HL_EINVAL, "bad target arguments");
+    if (!nodes_dev && rows > c.nnode) return mlp_err(nullptr, HL_EINVAL, "rows exceed the grid");
+    if (rows == 0) return HL_OK;
+    const int64_t n = (int64_t)rows * kOut;
+    k_targets<<<(unsigned)((n + 255) / 256), 256, 0, coarse->stream>>>(fine->p, (int)f.n[0], f.nnode, ratio, coarse->p,
+                                                                        (int)c.n[0], c.nnode, nodes_dev, rows,
+                                                                        1.0 / out_scale, T_dev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HL_OK : mlp_err(nullptr, HL_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_scale, float t_feature,
+                                   double out_scale)
+{
+    int rc = solver_ok(coarse);
+    if (rc) return rc;
+    rc = mlp_check(mlp);
+    if (rc) return rc;
+    const Shot &s = coarse->shots[0];
+    const int rows = (int)s.nnode;
+    // features (rows x kIn) live after the activations in one workspace
+    const int64_t per_row = 2 * kH + 2 * kOut + 2 * kH;
+    rc = ensure_rows(mlp, rows + ((int64_t)rows * kIn + per_row - 1) / per_row);
+    if (rc) return rc;
+    // order the correction after the solver's pending work
+    if (mlp->stream != coarse->stream) {
+        MLP_CK(mlp, cudaStreamSynchronize(coarse->stream));
+    }
+    const Work w = work_ptrs(mlp, rows);
+    float *X = w.dH1 + (int64_t)rows * kH;
+    const int64_t nx = (int64_t)rows * kIn;
+    k_features<<<(unsigned)((nx + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, coarse->u, (int)s.n[0], (int)s.n[1],
+                                                                       s.nnode, nullptr, rows, feat_scale, t_feature, X);
+    MLP_CK(mlp, cudaGetLastError());
+    MLP_CK(mlp, forward_into(mlp, X, rows, w, w.Y));
+    const int64_t ny = (int64_t)rows * kOut;
+    k_correct<<<(unsigned)((ny + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, s.nnode, w.Y, rows, out_scale);
+    MLP_CK(mlp, cudaGetLastError());
+    if (mlp->stream != coarse->stream) MLP_CK(mlp, cudaStreamSynchronize(mlp->stream));
+    return HL_OK;
+}

@@ -1,0 +1,77 @@
+// The solver handle (shared by the library's translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hl.h"
+#include "hl_internal.h"
+
+namespace hl {
+
+// tile (thread block) shapes the autotuner chooses from: (TX, TY)
+constexpr int kTiles[][2] = {{128, 1}, {256, 1}, {64, 2}, {32, 4}, {32, 8}, {64, 4}, {16, 8}, {16, 16}};
+constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+static_assert(kNumTiles == HL_NUM_TILES, "tile table and header disagree");
+
+struct Shot {
+    int64_t n[3] = {1, 1, 1};
+    double dt = 0.0;
+    double lam[3] = {0.0, 0.0, 0.0};
+    int64_t nnode = 0;
+    int64_t p_off = 0;   // element offset in the slot-major p array (and host p array)
+    int64_t u_off = 0;   // element offset in the slot-major u array (and host u array)
+};
+
+}  // namespace hl
+
+struct hl_solver {
+    int dim = 0, m = 0;
+    int64_t nq = 0;
+    std::vector<hl::Shot> shots;
+    int64_t p_elems = 0, u_elems = 0;           // totals over shots
+    double *p = nullptr, *u = nullptr;          // active device state, slot-major
+    double *p_own = nullptr, *u_own = nullptr;  // library-owned state
+    double *staging = nullptr;                  // host-layout staging, p_elems + u_elems
+    unsigned *status = nullptr;                 // device status word
+    unsigned *status_host = nullptr;            // pinned mirror
+    std::vector<double> coef;                   // n_shots dense tables (shot 0 first)
+    double *coef_dev = nullptr;
+    bool per_shot_coef = false;
+    // tiles
+    int tile = 0;
+    std::vector<hl::ShotDesc> shot_desc;
+    hl::ShotDesc *shot_desc_dev = nullptr;
+    int total_tiles = 0;
+    // streams and graph capture
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graph = false;
+    int64_t steps = 0;
+    bool poisoned = false;
+    int precision = HL_FP64;
+    int path = hl::PATH_AUTO;
+    std::string err;
+    // opt-in kernel timing (HL_OPT_TIMING)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        size_t first;
+        int64_t nsteps;
+        bool small;
+    };
+    std::vector<Pending> pending;
+    size_t ev_used = 0;
+    double t_p_ms = 0.0, t_u_ms = 0.0, t_small_ms = 0.0;
+    int64_t n_p = 0, n_u = 0, n_small = 0;
+    // point sources
+    hl::SourceDesc src;
+    int *src_node = nullptr, *src_shot = nullptr;
+    double *src_table = nullptr;
+};
+

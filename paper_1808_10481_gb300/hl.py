@@ -25,6 +25,7 @@ HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
 HL_NUM_TILES = 8
+HL_MLP_IN, HL_MLP_HIDDEN, HL_MLP_OUT, HL_MLP_NPARAMS = 288, 128, 16, 55568
 TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16)]
 CODE_NAMES = {0: "HL_OK", -1: "HL_EINVAL", -2: "HL_ENOMEM", -3: "HL_ECUDA", -4: "HL_ETIMEOUT",
               -5: "HL_ENONFINITE", -6: "HL_ESTATE"}
@@ -64,6 +65,17 @@ _SIGNATURES = [
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("hl_mlp_create", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_P)]),
+    ("hl_mlp_destroy", None, [_P]),
+    ("hl_mlp_last_error", ctypes.c_char_p, [_P]),
+    ("hl_mlp_set_stream", ctypes.c_int, [_P, _P]),
+    ("hl_mlp_params", ctypes.c_int, [_P, _P, _P, _P]),
+    ("hl_mlp_forward", ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    ("hl_mlp_loss_grad", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(_D)]),
+    ("hl_mlp_adam_step", ctypes.c_int, [_P, ctypes.c_float]),
+    ("hl_features", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
+    ("hl_targets", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _D, _P]),
+    ("hl_apply_correction", ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _D]),
     ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
 ]
@@ -294,3 +306,102 @@ def hl_info(h: Handle):
     nn, nq, st = _I64(), _I64(), _I64()
     _check(h, load().hl_info(h.ptr, ctypes.byref(nn), ctypes.byref(nq), ctypes.byref(st)))
     return nn.value, nq.value, st.value
+
+
+# ----------------------------------------------------------------------------- learned correction
+@dataclass
+class MLP:
+    ptr: ctypes.c_void_p
+
+
+def _mcheck(m: MLP, rc: int) -> None:
+    if rc != HL_OK:
+        raise HLError(rc, load().hl_mlp_last_error(m.ptr if m is not None else None).decode(errors="replace"))
+
+
+def _fptr(t, count: int):
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.float32" or not t.is_contiguous() \
+            or t.numel() < count:
+        raise ValueError("expected a contiguous float32 CUDA tensor of sufficient size")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _iptr(t, count: int):
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False) or str(t.dtype) != "torch.int32" or not t.is_contiguous() \
+            or t.numel() < count:
+        raise ValueError("expected a contiguous int32 CUDA tensor of sufficient size")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hl_mlp_create(seed: int) -> MLP:
+    out = _P()
+    rc = load().hl_mlp_create(int(seed), ctypes.byref(out))
+    if rc != HL_OK:
+        raise HLError(rc, load().hl_mlp_last_error(None).decode(errors="replace"))
+    return MLP(out)
+
+
+def hl_mlp_destroy(m: MLP) -> None:
+    if m is not None and m.ptr:
+        load().hl_mlp_destroy(m.ptr)
+        m.ptr = _P()
+
+
+def hl_mlp_last_error(m: MLP | None) -> str:
+    return load().hl_mlp_last_error(m.ptr if m is not None else None).decode(errors="replace")
+
+
+def hl_mlp_set_stream(m: MLP, stream) -> None:
+    raw = getattr(stream, "cuda_stream", stream)
+    _mcheck(m, load().hl_mlp_set_stream(m.ptr, ctypes.c_void_p(int(raw) if raw else 0)))
+
+
+def hl_mlp_params(m: MLP, set_params=None, want_grads: bool = False):
+    """Returns (params, grads or None) as float32 numpy arrays; set_params replaces the weights."""
+    p = np.empty(HL_MLP_NPARAMS, dtype=np.float32)
+    g = np.empty(HL_MLP_NPARAMS, dtype=np.float32) if want_grads else None
+    sp = None
+    if set_params is not None:
+        sp = np.ascontiguousarray(set_params, dtype=np.float32)
+        if sp.size != HL_MLP_NPARAMS:
+            raise ValueError("parameter block has the wrong size")
+        sp = ctypes.c_void_p(sp.ctypes.data)
+    _mcheck(m, load().hl_mlp_params(m.ptr, ctypes.c_void_p(p.ctypes.data), sp,
+                                    ctypes.c_void_p(g.ctypes.data) if g is not None else None))
+    return p, g
+
+
+def hl_mlp_forward(m: MLP, X, rows: int, Y) -> None:
+    _mcheck(m, load().hl_mlp_forward(m.ptr, _fptr(X, rows * HL_MLP_IN), int(rows), _fptr(Y, rows * HL_MLP_OUT)))
+
+
+def hl_mlp_loss_grad(m: MLP, X, T, rows: int, want_loss: bool = True):
+    loss = _D()
+    _mcheck(m, load().hl_mlp_loss_grad(m.ptr, _fptr(X, rows * HL_MLP_IN), _fptr(T, rows * HL_MLP_OUT), int(rows),
+                                       ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def hl_mlp_adam_step(m: MLP, lr: float) -> None:
+    _mcheck(m, load().hl_mlp_adam_step(m.ptr, ctypes.c_float(lr)))
+
+
+def hl_features(coarse: Handle, nodes, rows: int, feat_scale: float, t_feature: float, X) -> None:
+    rc = load().hl_features(coarse.ptr, _iptr(nodes, rows), int(rows), ctypes.c_float(feat_scale),
+                            ctypes.c_float(t_feature), _fptr(X, rows * HL_MLP_IN))
+    _mcheck(None, rc)
+
+
+def hl_targets(fine: Handle, ratio: int, coarse: Handle, nodes, rows: int, out_scale: float, T) -> None:
+    rc = load().hl_targets(fine.ptr, int(ratio), coarse.ptr, _iptr(nodes, rows), int(rows), float(out_scale),
+                           _fptr(T, rows * HL_MLP_OUT))
+    _mcheck(None, rc)
+
+
+def hl_apply_correction(coarse: Handle, m: MLP, feat_scale: float, t_feature: float, out_scale: float) -> None:
+    _mcheck(m, load().hl_apply_correction(coarse.ptr, m.ptr, ctypes.c_float(feat_scale), ctypes.c_float(t_feature),
+                                          float(out_scale)))

@@ -3,8 +3,8 @@
 Bar (stated in the workload definition): per field, max |gpu - oracle| / max |oracle|
 <= 1e-12 after the run, FP64 throughout.  Summation order differs between the two
 (butterflied fused operator vs. per-axis reconstruction + series), so results agree to
-rounding, not bitwise.  Runs of 20 steps or more are judged against the oracle's long
-double build (JUDGE): after hundreds of steps the binary64 oracle's own accumulated
+rounding, not bitwise.  Runs of 20 steps or more are judged against the oracle's
+double-double build (JUDGE): after hundreds of steps the binary64 oracle's own accumulated
 rounding (1.3e-12 on the 1000-step 1D workload, 2e-12 on the 200-step 2D one) is as
 large as the bar, so only a more precise judge can tell whether the GPU meets it.
 """
@@ -22,7 +22,7 @@ from paper_1808_10481_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
-JUDGE = "ld"
+JUDGE = "dd"
 EPS = np.finfo(np.float64).eps
 _ROWSUM = {}
 

@@ -447,21 +447,21 @@ def test_source_superposition():
 
 
 def test_long_double_build_agrees_with_binary64():
-    """The long double build (the judge of long GPU runs) is the same algorithm: on a short
+    """The double-double build (the judge of long GPU runs) is the same algorithm: on a short
     run the two builds agree to binary64 rounding, and on the 1000-step 1D workload they
     differ by no more than the binary64 build's accumulated rounding."""
     d, m, ncell = 2, 3, [12, 10]
     dt = I.cfl_dt(ncell)
     st = I.random_state(d, m, ncell, seed=31)
     p64, u64 = oracle.run(d, m, ncell, dt, st.p, st.u, 3)
-    pld, uld = oracle.run(d, m, ncell, dt, st.p, st.u, 3, prec="ld")
+    pld, uld = oracle.run(d, m, ncell, dt, st.p, st.u, 3, prec="dd")
     assert np.abs(p64 - pld).max() <= 1e-13 * np.abs(pld).max()
     assert np.abs(u64 - uld).max() <= 1e-13 * np.abs(uld).max()
     d, m, ncell = 1, 3, [64]
     dt = I.cfl_dt(ncell)
     st = I.standing_mode(d, m, ncell, dt, wave=[3])
     p64, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000)
-    pld, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="ld")
+    pld, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="dd")
     assert np.abs(p64 - pld).max() <= 1e-11 * np.abs(pld).max()
 
 
