@@ -187,8 +187,9 @@ def fp64_flops_per_node_step(dim, m):
     return 2 * fma + add
 
 
-def run_aux(args):
-    """Single-GPU measurements of the other workloads (one JSON line each)."""
+def run_aux(args, rank=0, world=1, dist=None):
+    """Measurements of the other workloads (one JSON line, printed by rank 0).  The batched
+    workload shards its shots over the ranks by cost; the others run on rank 0 only."""
     import numpy as np
     import torch
 
@@ -295,13 +296,19 @@ def run_aux(args):
     elif args.workload == "learned":
         out.update(run_learned(args))
     else:
+        from paper_1808_10481_gb300.sharding import max_over_ranks, shard_by_cost
         d, m, n_shots, lf = 2, 3, 64, 500
         rng = np.random.default_rng(2024)
-        sizes = [int(x) for x in rng.integers(128, 1025, size=n_shots)]
+        sizes_all = [int(x) for x in rng.integers(128, 1025, size=n_shots)]
+        x0_all = [list(rng.random(2)) for _ in range(n_shots)]
+        f0_all = [float(x) for x in rng.uniform(10.0, 20.0, size=n_shots)]
+        mine = shard_by_cost([n * n for n in sizes_all], world)[rank]
+        sizes = [sizes_all[i] for i in mine]
+        x0 = [x0_all[i] for i in mine]
+        f0 = [f0_all[i] for i in mine]
+        n_shots = len(mine)
         cells = [[n, n] for n in sizes]
         dts = [I.cfl_dt(c) for c in cells]
-        x0 = [list(rng.random(2)) for _ in range(n_shots)]
-        f0 = [float(x) for x in rng.uniform(10.0, 20.0, size=n_shots)]
         h = hl.hl_create_batch(d, m, cells, dts)
         hl.hl_set_stream(h, stream)
         best, tile_ms = hl.hl_autotune(h, 2)
@@ -313,20 +320,22 @@ def run_aux(args):
         hl.hl_step(h, lf)
         e1.record(stream)
         rc = hl.hl_sync(h)
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         hl.hl_destroy(h)
-        nnode = sum(n * n for n in sizes)
+        nnode = sum(n * n for n in sizes_all)
         dof = (d + 1) * (m + 1) ** d * nnode
         fl = fp64_flops_per_node_step(d, m) * nnode * lf
-        out.update({"workload": "batch", "value": dof * lf / (ms / 1e3), "ms_per_run": ms,
+        out.update({"workload": "batch", "n_gpus": world, "scaling": "strong (64 shots split by cost)", "value": dof * lf / (ms / 1e3), "ms_per_run": ms,
                     "config": {"workload": "64 independent 2D shots, n ~ U{128..1024} per axis (seed 2024), m=3, "
                                            "FP64, Ricker source per shot (f0 ~ U[10,20], sigma 0.01, seeded x0) "
                                            "from a zero field, 500 steps, one CUDA graph per run",
                                "total_nodes": nnode, "tile": hl.TILES[best], "tile_ms_per_step": tile_ms},
-                    "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                                 "unit": "TFLOP/s", "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS},
+                    "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12 / world,
+                                 "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                                 "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS / world},
                     "status": rc})
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
@@ -464,8 +473,16 @@ def main():
         run_reference(args, rank)
         return
     if args.workload != "2d":
-        if rank == 0:
-            run_aux(args)
+        import torch
+        torch.cuda.set_device(local_rank)
+        dist = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        if args.workload == "batch" or rank == 0:
+            run_aux(args, rank, world, dist)
+        if dist:
+            dist.destroy_process_group()
         return
 
     import numpy as np

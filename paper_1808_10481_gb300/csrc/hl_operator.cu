@@ -170,8 +170,11 @@ bool build_operator(int D, int m, const double lam[3], std::vector<double> &coef
                         const int b[3] = {b0, b1, b2};
                         const int K = b0 + b1 + b2;
                         int a[3] = {0, 0, 0};
-                        // W = 2 K!/(2K+1)! * prod_k [a_k!/(s_k! b_k!)] lam_k^(a_k - s_k)
-                        DD w = dd_div(dd_int(2 * ifact(K)), dd_int(ifact(2 * K + 1)));
+                        // W = 2 K!/(2K+1)! * prod_k [a_k!/(s_k! b_k!)] lam_k^(a_k - s_k);
+                        // 2 K!/(2K+1)! = 2 / ((K+1)(K+2)...(2K+1)), divided out one small
+                        // integer at a time ((2K+1)! itself overflows int64 for K >= 10)
+                        DD w = dd(2.0);
+                        for (int j = K + 1; j <= 2 * K + 1; ++j) w = dd_div(w, dd((double)j));
                         for (int k = 0; k < D; ++k) {
                             a[k] = sv[k] + 2 * b[k] + (k == i ? 1 : 0);
                             // a_k!/s_k! is an integer (a_k >= s_k) below 2^53
