@@ -72,6 +72,10 @@ static void release(hl_solver *h)
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->coef_dev) cudaFree(h->coef_dev);
     if (h->shot_desc_dev) cudaFree(h->shot_desc_dev);
+    if (h->Ph) cudaFree(h->Ph);
+    if (h->Pl) cudaFree(h->Pl);
+    if (h->Uh) cudaFree(h->Uh);
+    if (h->Ul) cudaFree(h->Ul);
     delete h;
 }
 
@@ -250,6 +254,17 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
                 if (std::fabs(s.lam[k] - h->shots[0].lam[k]) > 1e-12 * std::fabs(h->shots[0].lam[k]))
                     return set_err(h, HL_EINVAL, "mixed precision needs the same dt/h on every shot");
     }
+    if (mode != HL_FP64) {
+        // binary32 shadows of both fields (lo parts only for the compensated mode)
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        const size_t n = (size_t)h->p_elems;
+        if (!h->Ph) HL_CK(h, cudaMalloc(&h->Ph, n * sizeof(float)));
+        if (!h->Uh) HL_CK(h, cudaMalloc(&h->Uh, n * h->dim * sizeof(float)));
+        if (mode == HL_FP32_COMP) {
+            if (!h->Pl) HL_CK(h, cudaMalloc(&h->Pl, n * sizeof(float)));
+            if (!h->Ul) HL_CK(h, cudaMalloc(&h->Ul, n * h->dim * sizeof(float)));
+        }
+    }
     h->precision = mode;
     return HL_OK;
 }
@@ -416,6 +431,11 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.src = &h->src;
     a.step0 = h->steps;
     a.precision = h->precision;
+    a.Ph = h->Ph;
+    a.Pl = h->Pl;
+    a.Uh = h->Uh;
+    a.Ul = h->Ul;
+    a.p_elems = h->p_elems;
     return a;
 }
 

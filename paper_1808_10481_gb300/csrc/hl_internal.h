@@ -42,8 +42,9 @@ struct SourceDesc {
 double ricker(double t, double f0);
 bool build_source_table(int dim, int m, const int64_t *n, const double *x0, double sigma,
                         std::vector<int> &nodes, std::vector<double> &table);
+// Ph/Pl (may be NULL): binary32 shadows of P refreshed at the updated nodes
 cudaError_t launch_source(const SourceDesc &s, const ShotDesc *shots_dev, double *P, int nq, int64_t step,
-                          cudaStream_t st);
+                          cudaStream_t st, float *Ph = nullptr, float *Pl = nullptr);
 
 enum KernelPath { PATH_AUTO = 0, PATH_SMALL = 1, PATH_GRID = 2 };
 
@@ -73,6 +74,9 @@ struct LaunchFp64 {
     const SourceDesc *src;    // point sources injected after every p-half (may be NULL)
     int64_t step0;            // index of the first step (source time)
     int precision;            // HL_FP64 (0), HL_FP32 (1), HL_FP32_COMP (2)
+    // binary32 shadows of P and U for the mixed modes (lo only for HL_FP32_COMP)
+    float *Ph, *Pl, *Uh, *Ul;
+    int64_t p_elems;          // elements of P over all shots (U has dim times more)
 };
 
 cudaError_t launch_fp64_d1(const LaunchFp64 &a);

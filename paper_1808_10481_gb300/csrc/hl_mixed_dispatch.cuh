@@ -7,11 +7,12 @@
 namespace hl {
 
 template <int D, int M, bool COMP, int I>
-static void launch_u_split_f32(const LaunchFp64 &a, const CoefF32<D, M, COMP> &cf, dim3 grid, dim3 block)
+static void launch_u_split_mx(const LaunchFp64 &a, const CoefF32<D, M, COMP> &cf, dim3 grid, dim3 block)
 {
     if constexpr (I < D) {
-        k_u_half_f32<D, M, COMP, I, 1><<<grid, block, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cf, a.status);
-        launch_u_split_f32<D, M, COMP, I + 1>(a, cf, grid, block);
+        k_u_half_mx<D, M, COMP, I, 1><<<grid, block, 0, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots, a.n_shots,
+                                                                      cf, a.status);
+        launch_u_split_mx<D, M, COMP, I + 1>(a, cf, grid, block);
     }
 }
 
@@ -25,20 +26,26 @@ static cudaError_t run_mixed_t(const LaunchFp64 &a)
         cf.hi[c] = (float)v;
         if constexpr (COMP) cf.lo[c] = (float)(v - (double)cf.hi[c]);
     }
+    // shadows of the current binary64 state
+    const unsigned sb = 152 * 16;
+    k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.P, a.Ph, a.Pl, a.p_elems);
+    k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.U, a.Uh, a.Ul, a.p_elems * D);
     constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 192;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        k_p_half_f32<D, M, COMP><<<grid, block, 0, a.stream>>>(a.U, a.P, a.shots, a.n_shots, cf, a.status);
+        k_p_half_mx<D, M, COMP><<<grid, block, 0, a.stream>>>(a.Uh, a.Ul, a.P, a.Ph, a.Pl, a.shots, a.n_shots, cf,
+                                                               a.status);
         if (a.src && a.src->active) {
-            cudaError_t e = launch_source(*a.src, a.shots, a.P, S::NQ, a.step0 + st, a.stream);
+            cudaError_t e = launch_source(*a.src, a.shots, a.P, S::NQ, a.step0 + st, a.stream, a.Ph, a.Pl);
             if (e != cudaSuccess) return e;
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
         if constexpr (fused)
-            k_u_half_f32<D, M, COMP, 0, D><<<grid, block, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cf, a.status);
+            k_u_half_mx<D, M, COMP, 0, D><<<grid, block, 0, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots,
+                                                                         a.n_shots, cf, a.status);
         else
-            launch_u_split_f32<D, M, COMP, 0>(a, cf, grid, block);
+            launch_u_split_mx<D, M, COMP, 0>(a, cf, grid, block);
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();
@@ -49,6 +56,7 @@ static cudaError_t run_mixed(const LaunchFp64 &a)
 {
     if (a.nsteps <= 0) return cudaSuccess;
     if (a.used_small) *a.used_small = false;
+    if (!a.Ph || !a.Uh || (a.precision == 2 && (!a.Pl || !a.Ul))) return cudaErrorInvalidValue;
     if (a.precision == 2) return run_mixed_t<D, M, true>(a);
     return run_mixed_t<D, M, false>(a);
 }

@@ -71,6 +71,7 @@ struct hl_solver {
     int64_t n_p = 0, n_u = 0, n_small = 0;
     // point sources
     hl::SourceDesc src;
+    float *Ph = nullptr, *Pl = nullptr, *Uh = nullptr, *Ul = nullptr;  // mixed-precision shadows
     int *src_node = nullptr, *src_shot = nullptr;
     double *src_table = nullptr;
 };

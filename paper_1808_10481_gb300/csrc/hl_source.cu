@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "hl_internal.h"
+#include "hl_split.cuh"
 
 namespace hl {
 
@@ -97,18 +98,27 @@ bool build_source_table(int dim, int m, const int64_t *n, const double *x0, doub
 
 __global__ void k_source(double *__restrict__ P, const ShotDesc *__restrict__ shots, const int *__restrict__ node,
                          const int *__restrict__ shot, const double *__restrict__ table, int ne, int nq,
-                         SourceWeights w)
+                         SourceWeights w, float *__restrict__ Ph, float *__restrict__ Pl)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const int s = shot[e];
     const ShotDesc sd = shots[s];
-    double *Ps = P + sd.p_off + node[e];
-    for (int q = 0; q < nq; ++q) Ps[(int64_t)q * sd.nnode] += w.w[s] * table[(int64_t)e * nq + q];
+    const int64_t base = sd.p_off + node[e];
+    for (int q = 0; q < nq; ++q) {
+        const int64_t idx = base + (int64_t)q * sd.nnode;
+        const double v = P[idx] + w.w[s] * table[(int64_t)e * nq + q];
+        P[idx] = v;
+        if (Ph) {  // keep the mixed-precision shadows in step with the binary64 value
+            const FF sp = split_f64(v);
+            Ph[idx] = sp.hi;
+            if (Pl) Pl[idx] = sp.lo;
+        }
+    }
 }
 
 cudaError_t launch_source(const SourceDesc &s, const ShotDesc *shots_dev, double *P, int nq, int64_t step,
-                          cudaStream_t st)
+                          cudaStream_t st, float *Ph, float *Pl)
 {
     if (!s.active || s.n_entries == 0) return cudaSuccess;
     SourceWeights w;
@@ -116,7 +126,8 @@ cudaError_t launch_source(const SourceDesc &s, const ShotDesc *shots_dev, double
     for (size_t i = 0; i < (size_t)kMaxShots; ++i)
         w.w[i] = (i < ns && s.amp[i] != 0.0) ? s.dt[i] * s.amp[i] * ricker(((double)step + 0.5) * s.dt[i], s.f0[i])
                                             : 0.0;
-    k_source<<<(s.n_entries + 127) / 128, 128, 0, st>>>(P, shots_dev, s.node, s.shot, s.table, s.n_entries, nq, w);
+    k_source<<<(s.n_entries + 127) / 128, 128, 0, st>>>(P, shots_dev, s.node, s.shot, s.table, s.n_entries, nq, w,
+                                                        Ph, Pl);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,12 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 single CTA, 2 grid launches")
     ap.add_argument("--init", choices=["gaussian", "random", "zero"], default="random")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_comp"], default="fp64")
+    ap.add_argument("--mlp-rows", type=int, default=0,
+                    help="instead of stepping: this many rows of MLP training steps (loss, gradient, Adam)")
     args = ap.parse_args(argv)
+    if args.mlp_rows:
+        return run_mlp(args)
 
     import numpy as np
     import torch
@@ -56,6 +61,7 @@ def main(argv=None):
         hl.hl_set_stream(h, stream)
         if args.path:
             hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, args.path)
+        hl.hl_set_precision(h, {"fp64": hl.HL_FP64, "fp32": hl.HL_FP32, "fp32_comp": hl.HL_FP32_COMP}[args.precision])
         hl.hl_set_initial(h, p, u)
         if args.warmup:
             hl.hl_step(h, args.warmup)
@@ -70,10 +76,46 @@ def main(argv=None):
     finally:
         hl.hl_destroy(h)
     dof = (args.dim + 1) * (args.m + 1) ** args.dim * int(np.prod(ncell))
-    print(json.dumps({"dim": args.dim, "m": args.m, "n_cells": ncell, "steps": args.steps, "ms": ms,
+    print(json.dumps({"dim": args.dim, "m": args.m, "n_cells": ncell, "precision": args.precision,
+                      "steps": args.steps, "ms": ms,
                       "ms_per_step": ms / max(args.steps, 1), "dof_updates_per_s": dof * args.steps / (ms / 1e3),
                       "status": status}))
     return 0 if status == hl.HL_OK else 1
+
+
+def run_mlp(args):
+    """MLP training steps on seeded random rows (the learned correction's kernels)."""
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import hl
+
+    hl.load()
+    rows = args.mlp_rows
+    rng = np.random.default_rng(args.seed)
+    X = torch.from_numpy(rng.standard_normal((rows, hl.HL_MLP_IN)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.standard_normal((rows, hl.HL_MLP_OUT)).astype(np.float32)).cuda()
+    net = hl.hl_mlp_create(args.seed)
+    try:
+        stream = torch.cuda.current_stream()
+        hl.hl_mlp_set_stream(net, stream)
+        for _ in range(args.warmup):
+            hl.hl_mlp_loss_grad(net, X, T, rows, want_loss=False)
+            hl.hl_mlp_adam_step(net, 1e-3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            hl.hl_mlp_loss_grad(net, X, T, rows, want_loss=False)
+            hl.hl_mlp_adam_step(net, 1e-3)
+        e1.record(stream)
+        loss = hl.hl_mlp_loss_grad(net, X, T, rows)
+        ms = e0.elapsed_time(e1)
+    finally:
+        hl.hl_mlp_destroy(net)
+    flops = 3 * 2 * rows * (hl.HL_MLP_IN * hl.HL_MLP_HIDDEN + hl.HL_MLP_HIDDEN ** 2 + hl.HL_MLP_HIDDEN * hl.HL_MLP_OUT)
+    print(json.dumps({"mlp_rows": rows, "steps": args.steps, "ms_per_step": ms / max(args.steps, 1),
+                      "tflops": flops * args.steps / (ms / 1e3) / 1e12, "loss": loss}))
+    return 0
 
 
 if __name__ == "__main__":
