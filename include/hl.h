@@ -279,6 +279,32 @@ int hl_op_counts(int dim, int m, double *fma_per_node_step, double *add_per_node
  */
 int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
 
+/*
+ * hl_step_noalloc -- advance n_steps FP64 steps of one periodic grid held in
+ * caller-owned device buffers (device layout, as hl_bind_device), with no
+ * device allocation at all.  For callers that cannot call cudaMalloc: code
+ * living inside a device memory budget owned by another application,
+ * real-time loops that forbid allocation after start-up, or hosts whose
+ * allocator is locked while they run.  The paper has no counterpart; this is
+ * a deployment variant of hl_step.
+ *   dim, m, n_cells, dt : as hl_create; p_dev, u_dev : the state, updated in
+ *   place; cuda_stream : stream to run on (NULL = legacy default stream).
+ * The kernels' scratch (status word, grid descriptor and, when it does not fit
+ * the kernel parameter bank, the operator table) lives in one file-scope
+ * static device array of HL_NOALLOC_SCRATCH_BYTES, held by every GPU that
+ * loads the library until the process exits.  Operators larger than that
+ * (3D m = 3) are rejected with HL_EINVAL.  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.
+ * Every call shares the array and clears the status word it uses: calls that
+ * overlap on the GPU (other streams, other host threads) race on it.
+ * Synchronises the stream and returns HL_OK, HL_ENONFINITE, HL_EINVAL or
+ * HL_ECUDA; hl_last_error(NULL) describes a failure.  Host memory is used
+ * only to build the operator table.
+ */
+#define HL_NOALLOC_SCRATCH_BYTES 65536
+int hl_step_noalloc(int dim, int m, const int64_t *n_cells, double dt, double *p_dev, double *u_dev,
+                    int64_t n_steps, void *cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Learned coarse-grid correction (not in the paper).  A per-node multilayer
  * perceptron over a coarse 2D m = 3 solution predicts, for every primal node,

@@ -16,6 +16,8 @@ using namespace hl;
 
 static thread_local std::string g_create_error;
 
+void hl::set_handleless_error(const char *msg) { g_create_error = msg; }
+
 static int set_err(hl_solver *h, int code, const std::string &msg)
 {
     if (h)

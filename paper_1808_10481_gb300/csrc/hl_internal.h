@@ -86,6 +86,9 @@ cudaError_t launch_mixed_d1(const LaunchFp64 &a);  // precision 1 or 2, m <= 3
 cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 
+// message returned by hl_last_error(NULL) for calls that have no handle
+void set_handleless_error(const char *msg);
+
 // host-layout <-> device-layout copies, ncomp blocks of [nnode][nq] <-> [nq][nnode]
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int ncomp, int64_t nnode, int nq, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int ncomp, int64_t nnode, int nq, cudaStream_t st);

@@ -76,6 +76,7 @@ _SIGNATURES = [
     ("hl_features", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
     ("hl_targets", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _D, _P]),
     ("hl_apply_correction", ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _D]),
+    ("hl_step_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, _P, _P, _I64, _P]),
     ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
 ]
@@ -292,6 +293,21 @@ def hl_operator_table(dim: int, m: int, lam) -> np.ndarray:
     if rc != HL_OK:
         raise HLError(rc, hl_last_error(None))
     return out.reshape(dim, nq, nq)
+
+
+def hl_step_noalloc(dim: int, m: int, n_cells, dt: float, p_dev, u_dev, n_steps: int, stream=None) -> int:
+    """FP64 steps on caller-owned device buffers (device layout) with no device allocation.
+    Returns HL_OK or HL_ENONFINITE; raises on other failures."""
+    nnode = int(np.prod(n_cells))
+    nq = (m + 1) ** dim
+    nc = (_I64 * len(n_cells))(*[int(x) for x in n_cells])
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = load().hl_step_noalloc(int(dim), int(m), nc, float(dt), _dev_ptr(p_dev, nnode * nq),
+                                _dev_ptr(u_dev, dim * nnode * nq), int(n_steps),
+                                ctypes.c_void_p(int(raw) if raw else 0))
+    if rc not in (HL_OK, HL_ENONFINITE):
+        raise HLError(rc, hl_last_error(None))
+    return rc
 
 
 def hl_op_counts(dim: int, m: int):
