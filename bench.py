@@ -255,6 +255,7 @@ def run_aux(args, rank=0, world=1, dist=None):
             hl.hl_set_stream(h, stream)
             hl.hl_set_precision(h, mode)
             hl.hl_set_initial(h, st.p, st.u)
+            tile, _ = hl.hl_autotune(h, 1)
             hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -265,7 +266,7 @@ def run_aux(args, rank=0, world=1, dist=None):
             kt, kc = hl.hl_kernel_times(h)
             pg, ug, _, _ = hl.hl_get_fields(h)
             hl.hl_destroy(h)
-            r = {"value": dof * lf / (ms / 1e3), "ms_per_step": ms / lf,
+            r = {"value": dof * lf / (ms / 1e3), "ms_per_step": ms / lf, "tile": hl.TILES[tile],
                  "p_half_us": 1e3 * kt["p_half"] / max(kc["p_half"], 1),
                  "u_half_us": 1e3 * kt["u_half"] / max(kc["u_half"], 1)}
             if ex is not None:
@@ -509,6 +510,7 @@ def main():
     h = hl.hl_create(DIM, M, ncell, dt)
     hl.hl_set_stream(h, stream)
     hl.hl_set_initial(h, st.p, st.u)
+    tile, _ = hl.hl_autotune(h, 2)          # tile shape for this GPU and workload (untimed)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
@@ -605,6 +607,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dim": DIM, "m": M, "n_cells": ncell,
                        "leapfrog_steps_per_step": LF_STEPS, "l2": "flushed between timed steps (256 MiB write)",
+                       "tile": hl.TILES[tile],
                        "parallelism": f"replicas x{world}: one independently seeded problem per GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
             "gpu_launches": int(kcount["p_half"] + kcount["u_half"] + kcount["small"]),

@@ -135,80 +135,116 @@ __device__ __forceinline__ bool store_value(double *__restrict__ X, float *__res
     return !isfinite(v);
 }
 
-template <int D, int M, bool COMP>
-__global__ void __launch_bounds__(256)
-    k_p_half_mx(const float *__restrict__ Uh, const float *__restrict__ Ul, double *__restrict__ P,
-                float *__restrict__ Ph, float *__restrict__ Pl, const ShotDesc *__restrict__ shots, int n_shots,
-                CoefF32<D, M, COMP> cf, unsigned *status)
+// ---------------------------------------------------------------------------
+// One half-step of a mixed mode.  The partner field's shadows for the block's
+// tile plus its one-node halo are staged through shared memory, one partner
+// component at a time (a cooperative, coalesced load of every slot, then all
+// vertex reads from shared memory).
+//   PHALF: partner = U (D components), target = P, cell vertices j-1, j;
+//   else : partner = P, target = U components I0 .. I0+NI-1, vertices j, j+1.
+// Dynamic shared memory: NQ * R floats per shadow part, R = (TX+1)(TY+1)(2)
+// over the axes in use.
+template <int D>
+__device__ __forceinline__ int region_size()
 {
-    using S = Shape<D, M>;
-    int shot;
-    ShotDesc sd;
-    int64_t node;
-    if (!tile_node<D>(shots, n_shots, shot, sd, node)) return;
-    const GridDesc g{{sd.n[0], sd.n[1], sd.n[2]}, sd.nnode};
-    int vtx[S::NV];
-    vertex_nodes<D>(g, node, -1, vtx);
-    Acc<COMP> acc[S::NQ];
-#pragma unroll
-    for (int s = 0; s < S::NQ; ++s) acc[s].zero();
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-#pragma unroll
-        for (int l = 0; l < S::NQ; ++l) {
-            const int64_t off = sd.u_off + (int64_t)(i * S::NQ + l) * g.nnode;
-            Slot<D, COMP> x;
-            x.load(Uh + off, COMP ? Ul + off : nullptr, vtx);
-#pragma unroll
-            for (int s = 0; s < S::NQ; ++s)
-                if (coef_nonzero(D, S::n, i, s, l))
-                    x.madd(acc[s], cf, coef_index(S::NQ, i, l, s), bfly_pattern(D, S::n, i, s, l));
-        }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int s = 0; s < S::NQ; ++s)
-        bad |= store_value<COMP>(P, Ph, Pl, sd.p_off + (int64_t)s * g.nnode + node, acc[s].to_f64());
-    report_nonfinite(bad, status);
+    int r = blockDim.x + 1;
+    if (D >= 2) r *= blockDim.y + 1;
+    if (D >= 3) r *= 2;
+    return r;
 }
 
-template <int D, int M, bool COMP, int I0, int NI>
+template <int D, int M, bool COMP, bool PHALF, int I0, int NI>
 __global__ void __launch_bounds__(256)
-    k_u_half_mx(const float *__restrict__ Ph, const float *__restrict__ Pl, double *__restrict__ U,
-                float *__restrict__ Uh, float *__restrict__ Ul, const ShotDesc *__restrict__ shots, int n_shots,
-                CoefF32<D, M, COMP> cf, unsigned *status)
+    k_half_mx(const float *__restrict__ Sh, const float *__restrict__ Sl, double *__restrict__ X,
+              float *__restrict__ Xh, float *__restrict__ Xl, const ShotDesc *__restrict__ shots, int n_shots,
+              CoefF32<D, M, COMP> cf, unsigned *status)
 {
     using S = Shape<D, M>;
+    extern __shared__ float sm[];
     int shot;
     ShotDesc sd;
     int64_t node;
-    if (!tile_node<D>(shots, n_shots, shot, sd, node)) return;
-    const GridDesc g{{sd.n[0], sd.n[1], sd.n[2]}, sd.nnode};
-    int vtx[S::NV];
-    vertex_nodes<D>(g, node, 0, vtx);
-    Acc<COMP> acc[NI * S::NQ];
+    const bool active = tile_node<D>(shots, n_shots, shot, sd, node);
+    // tile origin (tile_node's arithmetic, for the whole block)
+    int t = blockIdx.x - sd.tile_begin;
+    const int x0 = (t % sd.tiles[0]) * blockDim.x;
+    t /= sd.tiles[0];
+    const int y0 = (t % sd.tiles[1]) * blockDim.y;
+    const int z0 = t / sd.tiles[1];
+    const int lo = PHALF ? -1 : 0;
+    const int RX = blockDim.x + 1, RY = D >= 2 ? blockDim.y + 1 : 1, RZ = D >= 3 ? 2 : 1;
+    const int R = RX * RY * RZ;
+    float *sh = sm;
+    float *sl = sm + S::NQ * R;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthr = blockDim.x * blockDim.y;
+    // this thread's vertex offsets inside the staged region
+    int vr[S::NV];
 #pragma unroll
-    for (int e = 0; e < NI * S::NQ; ++e) acc[e].zero();
-#pragma unroll
-    for (int l = 0; l < S::NQ; ++l) {
-        const int64_t off = sd.p_off + (int64_t)l * g.nnode;
-        Slot<D, COMP> x;
-        x.load(Ph + off, COMP ? Pl + off : nullptr, vtx);
-#pragma unroll
-        for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-            for (int s = 0; s < S::NQ; ++s)
-                if (coef_nonzero(D, S::n, I0 + ii, s, l))
-                    x.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
-                           bfly_pattern(D, S::n, I0 + ii, s, l));
+    for (int v = 0; v < S::NV; ++v) {
+        const int rx = threadIdx.x + (v & 1);
+        const int ry = D >= 2 ? threadIdx.y + ((v >> 1) & 1) : 0;
+        const int rz = D >= 3 ? ((v >> 2) & 1) : 0;
+        vr[v] = rx + RX * (ry + RY * rz);
     }
+    constexpr int NACC = PHALF ? S::NQ : NI * S::NQ;
+    Acc<COMP> acc[NACC];
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) acc[e].zero();
+    constexpr int NCOMP = PHALF ? D : 1;
+#pragma unroll
+    for (int c = 0; c < NCOMP; ++c) {
+        const int64_t coff = (PHALF ? sd.u_off : sd.p_off) + (int64_t)c * S::NQ * sd.nnode;
+        __syncthreads();  // the previous component's reads are done
+        for (int e = tid; e < S::NQ * R; e += nthr) {
+            const int slot = e / R, r = e % R;
+            int rx = r % RX, ry = (r / RX) % RY, rz = r / (RX * RY);
+            int gx = x0 + lo + rx, gy = y0 + lo + ry, gz = z0 + lo + rz;
+            gx += gx < 0 ? sd.n[0] : (gx >= sd.n[0] ? -sd.n[0] : 0);
+            if (D >= 2) gy += gy < 0 ? sd.n[1] : (gy >= sd.n[1] ? -sd.n[1] : 0); else gy = 0;
+            if (D >= 3) gz += gz < 0 ? sd.n[2] : (gz >= sd.n[2] ? -sd.n[2] : 0); else gz = 0;
+            const int64_t g = coff + (int64_t)slot * sd.nnode + gx + (int64_t)sd.n[0] * (gy + (int64_t)sd.n[1] * gz);
+            sh[e] = __ldg(Sh + g);
+            if constexpr (COMP) sl[e] = __ldg(Sl + g);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int l = 0; l < S::NQ; ++l) {
+                Slot<D, COMP> xs;
+#pragma unroll
+                for (int v = 0; v < S::NV; ++v) {
+                    if constexpr (COMP)
+                        xs.x[v] = FF{sh[l * R + vr[v]], sl[l * R + vr[v]]};
+                    else
+                        xs.x[v] = sh[l * R + vr[v]];
+                }
+                if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
+                if constexpr (PHALF) {
+#pragma unroll
+                    for (int s = 0; s < S::NQ; ++s)
+                        if (coef_nonzero(D, S::n, c, s, l))
+                            xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
+                } else {
+#pragma unroll
+                    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+                        for (int s = 0; s < S::NQ; ++s)
+                            if (coef_nonzero(D, S::n, I0 + ii, s, l))
+                                xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
+                                        bfly_pattern(D, S::n, I0 + ii, s, l));
+                }
+            }
+        }
+    }
+    if (!active) return;
     bool bad = false;
 #pragma unroll
-    for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-        for (int s = 0; s < S::NQ; ++s)
-            bad |= store_value<COMP>(U, Uh, Ul, sd.u_off + (int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node,
-                                     acc[ii * S::NQ + s].to_f64());
+    for (int e = 0; e < NACC; ++e) {
+        const int64_t idx = (PHALF ? sd.p_off + (int64_t)e * sd.nnode
+                                   : sd.u_off + (int64_t)(I0 * S::NQ + e) * sd.nnode) + node;
+        bad |= store_value<COMP>(X, Xh, Xl, idx, acc[e].to_f64());
+    }
     report_nonfinite(bad, status);
 }
 

@@ -6,14 +6,37 @@
 
 namespace hl {
 
+template <int D, int M, bool COMP, bool PHALF, int I0, int NI>
+static cudaError_t launch_half(const LaunchFp64 &a, const CoefF32<D, M, COMP> &cf, dim3 grid, dim3 block,
+                               size_t smem)
+{
+    auto kern = k_half_mx<D, M, COMP, PHALF, I0, NI>;
+    // allow up to the per-block maximum once per instantiation (not per launch,
+    // and so never from inside a stream capture after the first call)
+    static bool opted_in = false;
+    if (!opted_in) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        opted_in = true;
+    }
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (PHALF)
+        kern<<<grid, block, smem, a.stream>>>(a.Uh, a.Ul, a.P, a.Ph, a.Pl, a.shots, a.n_shots, cf, a.status);
+    else
+        kern<<<grid, block, smem, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots, a.n_shots, cf, a.status);
+    return cudaGetLastError();
+}
+
 template <int D, int M, bool COMP, int I>
-static void launch_u_split_mx(const LaunchFp64 &a, const CoefF32<D, M, COMP> &cf, dim3 grid, dim3 block)
+static cudaError_t launch_u_split_mx(const LaunchFp64 &a, const CoefF32<D, M, COMP> &cf, dim3 grid, dim3 block,
+                                     size_t smem)
 {
     if constexpr (I < D) {
-        k_u_half_mx<D, M, COMP, I, 1><<<grid, block, 0, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots, a.n_shots,
-                                                                      cf, a.status);
-        launch_u_split_mx<D, M, COMP, I + 1>(a, cf, grid, block);
+        cudaError_t e = launch_half<D, M, COMP, false, I, 1>(a, cf, grid, block, smem);
+        if (e != cudaSuccess) return e;
+        return launch_u_split_mx<D, M, COMP, I + 1>(a, cf, grid, block, smem);
     }
+    return cudaSuccess;
 }
 
 template <int D, int M, bool COMP>
@@ -30,22 +53,27 @@ static cudaError_t run_mixed_t(const LaunchFp64 &a)
     const unsigned sb = 152 * 16;
     k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.P, a.Ph, a.Pl, a.p_elems);
     k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.U, a.Uh, a.Ul, a.p_elems * D);
-    constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 192;
+    // keep all D float-float accumulator blocks of the u-half in registers only when small
+    constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 64;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
+    int region = a.tx + 1;
+    if (D >= 2) region *= a.ty + 1;
+    if (D >= 3) region *= 2;
+    const size_t smem = (size_t)S::NQ * region * sizeof(float) * (COMP ? 2 : 1);
+    cudaError_t e;
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        k_p_half_mx<D, M, COMP><<<grid, block, 0, a.stream>>>(a.Uh, a.Ul, a.P, a.Ph, a.Pl, a.shots, a.n_shots, cf,
-                                                               a.status);
+        if ((e = launch_half<D, M, COMP, true, 0, 1>(a, cf, grid, block, smem)) != cudaSuccess) return e;
         if (a.src && a.src->active) {
-            cudaError_t e = launch_source(*a.src, a.shots, a.P, S::NQ, a.step0 + st, a.stream, a.Ph, a.Pl);
-            if (e != cudaSuccess) return e;
+            if ((e = launch_source(*a.src, a.shots, a.P, S::NQ, a.step0 + st, a.stream, a.Ph, a.Pl)) != cudaSuccess)
+                return e;
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
         if constexpr (fused)
-            k_u_half_mx<D, M, COMP, 0, D><<<grid, block, 0, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots,
-                                                                         a.n_shots, cf, a.status);
+            e = launch_half<D, M, COMP, false, 0, D>(a, cf, grid, block, smem);
         else
-            launch_u_split_mx<D, M, COMP, 0>(a, cf, grid, block);
+            e = launch_u_split_mx<D, M, COMP, 0>(a, cf, grid, block, smem);
+        if (e != cudaSuccess) return e;
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();
