@@ -137,20 +137,39 @@ __device__ __forceinline__ bool store_value(double *__restrict__ X, float *__res
 
 // ---------------------------------------------------------------------------
 // One half-step of a mixed mode.  The partner field's shadows for the block's
-// tile plus its one-node halo are staged through shared memory, one partner
-// component at a time (a cooperative, coalesced load of every slot, then all
-// vertex reads from shared memory).
+// tile plus its one-node halo are staged through shared memory LC slots at a
+// time, in a two-buffer cp.async pipeline: while the block contracts one
+// stage (component c, slots l0 .. l0+LC-1) the next stage is in flight.
 //   PHALF: partner = U (D components), target = P, cell vertices j-1, j;
 //   else : partner = P, target = U components I0 .. I0+NI-1, vertices j, j+1.
-// Dynamic shared memory: NQ * R floats per shadow part, R = (TX+1)(TY+1)(2)
-// over the axes in use.
+// The staged region is (TX+1)(TY+1)(2) nodes over the axes in use; the
+// offset of each region node inside a slot is computed once per block and
+// kept in shared memory after the two buffers.
+template <int D, int M>
+struct MixedStage {
+    static constexpr int NQ = Shape<D, M>::NQ;
+    static constexpr int LC = M + 1;     // slots per stage (divides NQ)
+    static constexpr int NCH = NQ / LC;  // stages per component
+};
 template <int D>
-__device__ __forceinline__ int region_size()
+__host__ __device__ __forceinline__ int region_nodes(int tx, int ty)
 {
-    int r = blockDim.x + 1;
-    if (D >= 2) r *= blockDim.y + 1;
+    int r = tx + 1;
+    if (D >= 2) r *= ty + 1;
     if (D >= 3) r *= 2;
     return r;
+}
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 template <int D, int M, bool COMP, bool PHALF, int I0, int NI>
@@ -160,6 +179,10 @@ __global__ void __launch_bounds__(256)
               CoefF32<D, M, COMP> cf, unsigned *status)
 {
     using S = Shape<D, M>;
+    using G = MixedStage<D, M>;
+    constexpr int NCOMP = PHALF ? D : 1;
+    constexpr int NST = NCOMP * G::NCH;
+    constexpr int NPART = COMP ? 2 : 1;
     extern __shared__ float sm[];
     int shot;
     ShotDesc sd;
@@ -172,13 +195,22 @@ __global__ void __launch_bounds__(256)
     const int y0 = (t % sd.tiles[1]) * blockDim.y;
     const int z0 = t / sd.tiles[1];
     const int lo = PHALF ? -1 : 0;
-    const int RX = blockDim.x + 1, RY = D >= 2 ? blockDim.y + 1 : 1, RZ = D >= 3 ? 2 : 1;
-    const int R = RX * RY * RZ;
-    float *sh = sm;
-    float *sl = sm + S::NQ * R;
+    const int RX = blockDim.x + 1, RY = D >= 2 ? blockDim.y + 1 : 1;
+    const int R = region_nodes<D>(blockDim.x, blockDim.y);
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nthr = blockDim.x * blockDim.y;
-    // this thread's vertex offsets inside the staged region
+    // offsets inside one slot of every region node, once per block; stored
+    // after the two pipeline buffers
+    int *soff = reinterpret_cast<int *>(sm + (size_t)2 * NPART * G::LC * R);
+    for (int r = tid; r < R; r += nthr) {
+        int gx = x0 + lo + r % RX, gy = y0 + lo + (r / RX) % RY, gz = z0 + lo + r / (RX * RY);
+        gx += gx < 0 ? sd.n[0] : (gx >= sd.n[0] ? -sd.n[0] : 0);
+        if (D >= 2) gy += gy < 0 ? sd.n[1] : (gy >= sd.n[1] ? -sd.n[1] : 0); else gy = 0;
+        if (D >= 3) gz += gz < 0 ? sd.n[2] : (gz >= sd.n[2] ? -sd.n[2] : 0); else gz = 0;
+        soff[r] = gx + sd.n[0] * (gy + sd.n[1] * gz);
+    }
+    __syncthreads();
+    // this thread's cell vertices inside the region
     int vr[S::NV];
 #pragma unroll
     for (int v = 0; v < S::NV; ++v) {
@@ -187,55 +219,86 @@ __global__ void __launch_bounds__(256)
         const int rz = D >= 3 ? ((v >> 2) & 1) : 0;
         vr[v] = rx + RX * (ry + RY * rz);
     }
+    // stage st (component st / NCH, slots (st % NCH) * LC ...) holds the
+    // partner's slots st * LC .. st * LC + LC - 1; it goes to buffer st & 1.
+    // The source pointers advance one stage at a time and are hidden from the
+    // optimiser, so no per-stage address is precomputed and kept live.
+    const int64_t base = PHALF ? sd.u_off : sd.p_off;
+    const int64_t stage_stride = (int64_t)G::LC * sd.nnode;
+    const float *nh = Sh + base;
+    const float *nl = COMP ? Sl + base : nullptr;
+    auto prefetch = [&](int st) {
+        float *bh = sm + (size_t)((st & 1) * NPART) * G::LC * R;
+        // a rolled loop over the region: few live addresses at a time
+#pragma unroll 1
+        for (int r = tid; r < R; r += nthr) {
+            const int g = soff[r];
+#pragma unroll
+            for (int j = 0; j < G::LC; ++j) {
+                const int64_t so = (int64_t)j * sd.nnode + g;
+                cp_async4(bh + j * R + r, nh + so);
+                if constexpr (COMP) cp_async4(bh + (G::LC + j) * R + r, nl + so);
+            }
+        }
+        cp_async_commit();
+        nh += stage_stride;
+        asm volatile("" : "+l"(nh));
+        if constexpr (COMP) {
+            nl += stage_stride;
+            asm volatile("" : "+l"(nl));
+        }
+    };
     constexpr int NACC = PHALF ? S::NQ : NI * S::NQ;
     Acc<COMP> acc[NACC];
 #pragma unroll
     for (int e = 0; e < NACC; ++e) acc[e].zero();
-    constexpr int NCOMP = PHALF ? D : 1;
+    prefetch(0);
 #pragma unroll
-    for (int c = 0; c < NCOMP; ++c) {
-        const int64_t coff = (PHALF ? sd.u_off : sd.p_off) + (int64_t)c * S::NQ * sd.nnode;
-        __syncthreads();  // the previous component's reads are done
-        for (int e = tid; e < S::NQ * R; e += nthr) {
-            const int slot = e / R, r = e % R;
-            int rx = r % RX, ry = (r / RX) % RY, rz = r / (RX * RY);
-            int gx = x0 + lo + rx, gy = y0 + lo + ry, gz = z0 + lo + rz;
-            gx += gx < 0 ? sd.n[0] : (gx >= sd.n[0] ? -sd.n[0] : 0);
-            if (D >= 2) gy += gy < 0 ? sd.n[1] : (gy >= sd.n[1] ? -sd.n[1] : 0); else gy = 0;
-            if (D >= 3) gz += gz < 0 ? sd.n[2] : (gz >= sd.n[2] ? -sd.n[2] : 0); else gz = 0;
-            const int64_t g = coff + (int64_t)slot * sd.nnode + gx + (int64_t)sd.n[0] * (gy + (int64_t)sd.n[1] * gz);
-            sh[e] = __ldg(Sh + g);
-            if constexpr (COMP) sl[e] = __ldg(Sl + g);
+    for (int st = 0; st < NST; ++st) {
+        if (st + 1 < NST) {
+            prefetch(st + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        __syncthreads();
+        __syncthreads();  // stage st is visible to the whole block
         if (active) {
+            const int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
+            const float *bh = sm + (size_t)((st & 1) * NPART) * G::LC * R;
 #pragma unroll
-            for (int l = 0; l < S::NQ; ++l) {
-                Slot<D, COMP> xs;
+            for (int j = 0; j < G::LC; ++j) {
+                const int l = l0 + j;
+                {
+                    // one slot at a time: keeps the shared-memory reads of
+                    // later slots from being hoisted (register pressure)
+                    asm volatile("" ::: "memory");
+                    Slot<D, COMP> xs;
 #pragma unroll
-                for (int v = 0; v < S::NV; ++v) {
-                    if constexpr (COMP)
-                        xs.x[v] = FF{sh[l * R + vr[v]], sl[l * R + vr[v]]};
-                    else
-                        xs.x[v] = sh[l * R + vr[v]];
-                }
-                if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
-                if constexpr (PHALF) {
-#pragma unroll
-                    for (int s = 0; s < S::NQ; ++s)
-                        if (coef_nonzero(D, S::n, c, s, l))
-                            xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
-                } else {
-#pragma unroll
-                    for (int ii = 0; ii < NI; ++ii)
+                    for (int v = 0; v < S::NV; ++v) {
+                        if constexpr (COMP)
+                            xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
+                        else
+                            xs.x[v] = bh[j * R + vr[v]];
+                    }
+                    if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
+                    if constexpr (PHALF) {
 #pragma unroll
                         for (int s = 0; s < S::NQ; ++s)
-                            if (coef_nonzero(D, S::n, I0 + ii, s, l))
-                                xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
-                                        bfly_pattern(D, S::n, I0 + ii, s, l));
+                            if (coef_nonzero(D, S::n, c, s, l))
+                                xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
+                    } else {
+#pragma unroll
+                        for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+                            for (int s = 0; s < S::NQ; ++s)
+                                if (coef_nonzero(D, S::n, I0 + ii, s, l))
+                                    xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
+                                            bfly_pattern(D, S::n, I0 + ii, s, l));
+                    }
                 }
             }
         }
+        __syncthreads();  // buffer st & 1 is free for stage st + 2
     }
     if (!active) return;
     bool bad = false;

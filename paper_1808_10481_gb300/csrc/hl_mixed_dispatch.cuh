@@ -1,6 +1,8 @@
 // Launch logic of the mixed-precision kernels (included once per dimension).
 #pragma once
 
+#include <atomic>
+
 #include "hl_internal.h"
 #include "hl_mixed.cuh"
 
@@ -11,13 +13,17 @@ static cudaError_t launch_half(const LaunchFp64 &a, const CoefF32<D, M, COMP> &c
                                size_t smem)
 {
     auto kern = k_half_mx<D, M, COMP, PHALF, I0, NI>;
-    // allow up to the per-block maximum once per instantiation (not per launch,
-    // and so never from inside a stream capture after the first call)
-    static bool opted_in = false;
-    if (!opted_in) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // allow up to the per-block maximum once per instantiation and device (not
+    // per launch, and so never from inside a stream capture after the first call)
+    static std::atomic<uint64_t> opted_in{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(opted_in.load() & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        opted_in = true;
+        opted_in.fetch_or(bit);
     }
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     if (PHALF)
@@ -56,10 +62,10 @@ static cudaError_t run_mixed_t(const LaunchFp64 &a)
     // keep all D float-float accumulator blocks of the u-half in registers only when small
     constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 64;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
-    int region = a.tx + 1;
-    if (D >= 2) region *= a.ty + 1;
-    if (D >= 3) region *= 2;
-    const size_t smem = (size_t)S::NQ * region * sizeof(float) * (COMP ? 2 : 1);
+    const int region = region_nodes<D>(a.tx, a.ty);
+    // two pipeline buffers of LC slots each (hi, and lo for the compensated
+    // mode), then one offset per region node
+    const size_t smem = ((size_t)2 * MixedStage<D, M>::LC * (COMP ? 2 : 1) + 1) * region * sizeof(float);
     cudaError_t e;
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);

@@ -35,29 +35,35 @@ constexpr int kIn = HL_MLP_IN, kH = HL_MLP_HIDDEN, kOut = HL_MLP_OUT;
 // ---------------------------------------------------------------------------
 // C[M x N] = A[M x K] B[K x N] (+ bias[n]) (relu) ; element (r, c) of a matrix X
 // is X.p[r * X.rs + c * X.cs], so transposes are free.  64x64 block tile,
-// 4 warps of 32x32, K staged 32 at a time through shared memory as BF16.
+// 4 warps of 32x32, K staged 32 at a time through shared memory as BF16 (A as
+// [m][k], B transposed as [n][k], so every fragment register is one 32-bit
+// shared load).  Global loads run along whichever index is contiguous.
+// Split-K: block z covers K range [z*kc, (z+1)*kc) and writes its partial sums
+// to part[z]; k_gemm_reduce adds them in a fixed order (deterministic).
 struct Mat {
     const float *p;
     int64_t rs, cs;
 };
 
-constexpr int BM = 64, BN = 64, BK = 32;
+constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+__device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p)
 {
-    const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    return *reinterpret_cast<const uint32_t *>(p);
 }
 
 __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ C, int64_t ldc, int M, int N, int K,
-                                              const float *__restrict__ bias, int relu)
+                                              int kc, const float *__restrict__ bias, int relu,
+                                              float *__restrict__ part)
 {
-    __shared__ float As[BM][BK + 1];
-    __shared__ float Bs[BK][BN + 1];
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
+    __shared__ __align__(16) __nv_bfloat16 Bt[BN][BK + PADK];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * kc, kend = min(K, kbeg + kc);
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const bool a_kfast = A.cs == 1, b_nfast = B.cs == 1;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -65,16 +71,18 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         for (int e = tid; e < BM * BK; e += 128) {
-            const int r = e / BK, c = e % BK;
+            const int r = a_kfast ? e / BK : e % BM, c = a_kfast ? e % BK : e / BM;
             const int gr = m0 + r, gc = k0 + c;
-            As[r][c] = (gr < M && gc < K) ? A.p[(int64_t)gr * A.rs + (int64_t)gc * A.cs] : 0.f;
+            const float v = (gr < M && gc < kend) ? A.p[(int64_t)gr * A.rs + (int64_t)gc * A.cs] : 0.f;
+            As[r][c] = __float2bfloat16_rn(v);
         }
         for (int e = tid; e < BK * BN; e += 128) {
-            const int r = e / BN, c = e % BN;
+            const int r = b_nfast ? e / BN : e % BK, c = b_nfast ? e % BN : e / BK;
             const int gr = k0 + r, gc = n0 + c;
-            Bs[r][c] = (gr < K && gc < N) ? B.p[(int64_t)gr * B.rs + (int64_t)gc * B.cs] : 0.f;
+            const float v = (gr < kend && gc < N) ? B.p[(int64_t)gr * B.rs + (int64_t)gc * B.cs] : 0.f;
+            Bt[c][r] = __float2bfloat16_rn(v);
         }
         __syncthreads();
 #pragma unroll
@@ -83,16 +91,16 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int r = wm + i * 16 + g;
-                af[i][0] = pack_bf16(As[r][kk + 2 * t], As[r][kk + 2 * t + 1]);
-                af[i][1] = pack_bf16(As[r + 8][kk + 2 * t], As[r + 8][kk + 2 * t + 1]);
-                af[i][2] = pack_bf16(As[r][kk + 2 * t + 8], As[r][kk + 2 * t + 9]);
-                af[i][3] = pack_bf16(As[r + 8][kk + 2 * t + 8], As[r + 8][kk + 2 * t + 9]);
+                af[i][0] = lds_pair(&As[r][kk + 2 * t]);
+                af[i][1] = lds_pair(&As[r + 8][kk + 2 * t]);
+                af[i][2] = lds_pair(&As[r][kk + 2 * t + 8]);
+                af[i][3] = lds_pair(&As[r + 8][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = wn + j * 8 + g;
-                bf[j][0] = pack_bf16(Bs[kk + 2 * t][c], Bs[kk + 2 * t + 1][c]);
-                bf[j][1] = pack_bf16(Bs[kk + 2 * t + 8][c], Bs[kk + 2 * t + 9][c]);
+                bf[j][0] = lds_pair(&Bt[c][kk + 2 * t]);
+                bf[j][1] = lds_pair(&Bt[c][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -106,6 +114,8 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
         }
         __syncthreads();
     }
+    float *out = part ? part + (int64_t)blockIdx.z * M * N : C;
+    const int64_t ld = part ? N : ldc;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -116,19 +126,46 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
                 const int c = n0 + wn + j * 8 + 2 * t + (e & 1);
                 if (r < M && c < N) {
                     float v = acc[i][j][e];
-                    if (bias) v += bias[c];
-                    if (relu) v = fmaxf(v, 0.f);
-                    C[(int64_t)r * ldc + c] = v;
+                    if (!part) {
+                        if (bias) v += bias[c];
+                        if (relu) v = fmaxf(v, 0.f);
+                    }
+                    out[(int64_t)r * ld + c] = v;
                 }
             }
 }
 
+__global__ void k_gemm_reduce(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C,
+                              int64_t ldc, const float *__restrict__ bias, int relu)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += part[(int64_t)z * M * N + e];
+    const int r = (int)(e / N), c = (int)(e % N);
+    if (bias) v += bias[c];
+    if (relu) v = fmaxf(v, 0.f);
+    C[(int64_t)r * ldc + c] = v;
+}
+
+// split-K workspace is owned by the caller (the network handle): splits*M*N floats
 static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K, const float *bias, int relu,
-                        cudaStream_t st)
+                        cudaStream_t st, float *work = nullptr, int64_t work_floats = 0)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-    k_gemm<<<grid, 128, 0, st>>>(A, B, C, ldc, M, N, K, bias, relu);
+    const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    int splits = 1;
+    // few output tiles and a long K (weight gradients over the batch): split K
+    while (work && tiles * splits < 2 * 152 && K / (splits * 2) >= 4 * BK &&
+           (int64_t)(splits * 2) * M * N <= work_floats)
+        splits *= 2;
+    const int kc = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)splits);
+    k_gemm<<<grid, 128, 0, st>>>(A, B, C, ldc, M, N, K, kc, bias, relu, splits > 1 ? work : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    const int64_t n = (int64_t)M * N;
+    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(work, splits, M, N, C, ldc, bias, relu);
     return cudaGetLastError();
 }
 
@@ -266,6 +303,7 @@ static_assert(N_PARAMS == HL_MLP_NPARAMS, "parameter count and header disagree")
 struct hl_mlp {
     float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // N_PARAMS each
     float *work = nullptr;   // per-row activations: H1, H2, Y, dY, dH2, dH1
+    float *splitk = nullptr; // split-K partial sums of the weight gradients
     int64_t rows_cap = 0;
     double *loss = nullptr;  // device
     double *loss_host = nullptr;
@@ -276,6 +314,7 @@ struct hl_mlp {
 };
 
 static thread_local std::string g_mlp_error;
+static constexpr int64_t kSplitKFloats = (int64_t)64 * kIn * kH;  // 64 splits of the largest gradient
 
 static int mlp_err(hl_mlp *h, int code, const std::string &msg)
 {
@@ -359,6 +398,7 @@ extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
         (e = cudaMalloc(&h->m1, N_PARAMS * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->m2, N_PARAMS * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->loss, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->splitk, kSplitKFloats * sizeof(float))) != cudaSuccess ||
         (e = cudaMallocHost(&h->loss_host, sizeof(double))) != cudaSuccess) {
         std::string msg = std::string("mlp set-up failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -393,6 +433,7 @@ extern "C" void hl_mlp_destroy(hl_mlp *h)
     cudaFree(h->m1);
     cudaFree(h->m2);
     cudaFree(h->work);
+    cudaFree(h->splitk);
     cudaFree(h->loss);
     if (h->loss_host) cudaFreeHost(h->loss_host);
     delete h;
@@ -452,17 +493,20 @@ extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_de
     k_mse<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, T_dev, w.dY, ny, h->loss);
     MLP_CK(h, cudaGetLastError());
     // layer 3
-    MLP_CK(h, gemm({w.H2, 1, kH}, {w.dY, kOut, 1}, h->g + OFF_W3, kOut, kH, kOut, rows, nullptr, 0, st));
+    MLP_CK(h, gemm({w.H2, 1, kH}, {w.dY, kOut, 1}, h->g + OFF_W3, kOut, kH, kOut, rows, nullptr, 0, st, h->splitk,
+                   kSplitKFloats));
     k_colsum<<<kOut, 256, 0, st>>>(w.dY, h->g + OFF_B3, rows, kOut);
     MLP_CK(h, gemm({w.dY, kOut, 1}, {h->w + OFF_W3, 1, kOut}, w.dH2, kH, rows, kH, kOut, nullptr, 0, st));
     k_relu_mask<<<blocks_for((int64_t)rows * kH, 256), 256, 0, st>>>(w.dH2, w.H2, (int64_t)rows * kH);
     // layer 2
-    MLP_CK(h, gemm({w.H1, 1, kH}, {w.dH2, kH, 1}, h->g + OFF_W2, kH, kH, kH, rows, nullptr, 0, st));
+    MLP_CK(h, gemm({w.H1, 1, kH}, {w.dH2, kH, 1}, h->g + OFF_W2, kH, kH, kH, rows, nullptr, 0, st, h->splitk,
+                   kSplitKFloats));
     k_colsum<<<kH, 256, 0, st>>>(w.dH2, h->g + OFF_B2, rows, kH);
     MLP_CK(h, gemm({w.dH2, kH, 1}, {h->w + OFF_W2, 1, kH}, w.dH1, kH, rows, kH, kH, nullptr, 0, st));
     k_relu_mask<<<blocks_for((int64_t)rows * kH, 256), 256, 0, st>>>(w.dH1, w.H1, (int64_t)rows * kH);
     // layer 1
-    MLP_CK(h, gemm({X_dev, 1, kIn}, {w.dH1, kH, 1}, h->g + OFF_W1, kH, kIn, kH, rows, nullptr, 0, st));
+    MLP_CK(h, gemm({X_dev, 1, kIn}, {w.dH1, kH, 1}, h->g + OFF_W1, kH, kIn, kH, rows, nullptr, 0, st, h->splitk,
+                   kSplitKFloats));
     k_colsum<<<kH, 256, 0, st>>>(w.dH1, h->g + OFF_B1, rows, kH);
     MLP_CK(h, cudaGetLastError());
     if (loss) {
