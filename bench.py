@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hl", "reference"], default="hl")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-seeds", type=int, default=96, help="learned workload: training seeds")
+    ap.add_argument("--test-seeds", type=int, default=32, help="learned workload: held-out seeds")
     ap.add_argument("--workload", choices=["2d", "1d", "3d", "batch", "mixed3d", "mixed2d", "learned"], default="2d",
                     help="2d: the headline line; the others measure further rows of the solver")
     return ap.parse_args()
@@ -295,7 +297,7 @@ def run_aux(args, rank=0, world=1, dist=None):
                     "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
                     "modes": modes})
     elif args.workload == "learned":
-        out.update(run_learned(args))
+        out.update(run_learned(args, n_train=args.train_seeds, n_test=args.test_seeds))
     else:
         from paper_1808_10481_gb300.sharding import max_over_ranks, shard_by_cost
         d, m, n_shots, lf = 2, 3, 64, 500
@@ -382,34 +384,25 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
         return hc, hf, t0.elapsed_time(t1), t1.elapsed_time(t2)
 
     gen_rng = np.random.default_rng(0)
-    Xs, Ts, held = [], [], []
+    per_seed = 16384
+    n = n_train * per_seed
+    X = torch.empty((n, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
+    T = torch.empty((n, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
     t_coarse = t_fine = 0.0
     wall = time.perf_counter()
-    for i in range(n_train + n_test):
+    for i in range(n_train):
         hc, hf, tc, tf = pair(seed0 + i)
         t_coarse += tc
         t_fine += tf
-        if i < n_train:
-            nodes = torch.from_numpy(gen_rng.choice(rows, 16384, replace=False).astype(np.int32)).to(dev)
-            X = torch.empty((16384, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
-            T = torch.empty((16384, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
-            hl.hl_features(hc, nodes, 16384, 1.0, 0.0, X)
-            hl.hl_targets(hf, r, hc, nodes, 16384, 1.0, T)
-            Xs.append(X)
-            Ts.append(T)
-            hl.hl_destroy(hc)
-            hl.hl_destroy(hf)
-        else:
-            T = torch.empty((rows, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
-            hl.hl_targets(hf, r, hc, None, rows, 1.0, T)
-            held.append((hc, hf, T))
+        nodes = torch.from_numpy(gen_rng.choice(rows, per_seed, replace=False).astype(np.int32)).to(dev)
+        hl.hl_features(hc, nodes, per_seed, 1.0, 0.0, X[i * per_seed:(i + 1) * per_seed])
+        hl.hl_targets(hf, r, hc, nodes, per_seed, 1.0, T[i * per_seed:(i + 1) * per_seed])
+        hl.hl_destroy(hc)
+        hl.hl_destroy(hf)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - wall
-    X = torch.cat(Xs)
-    T = torch.cat(Ts)
     out_scale = float(T.pow(2).mean().sqrt())
-    T = T / out_scale
-    n = X.shape[0]
+    T /= out_scale
     net = hl.hl_mlp_create(7)
     hl.hl_mlp_set_stream(net, stream)
     g = torch.Generator(device="cpu").manual_seed(0)
@@ -423,22 +416,28 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
     e1.record(stream)
     final_loss = hl.hl_mlp_loss_grad(net, X[:65536].contiguous(), T[:65536].contiguous(), min(n, 65536))
     train_ms = e0.elapsed_time(e1)
+    del X, T
+    # held-out seeds, one pair at a time: plain error, correction, corrected error
     plain = corr = 0.0
     plain0 = corr0 = 0.0
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     corr_ms = 0.0
-    for hc, hf, Tt in held:
+    Tt = torch.empty((rows, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
+    for i in range(n_test):
+        hc, hf, tc, tf = pair(seed0 + n_train + i)
+        t_coarse += tc
+        t_fine += tf
+        hl.hl_targets(hf, r, hc, None, rows, 1.0, Tt)
         plain += float(Tt.pow(2).sum())
         plain0 += float(Tt[:, 0].pow(2).sum())
         e2.record(stream)
         hl.hl_apply_correction(hc, net, 1.0, 0.0, out_scale)
         e3.record(stream)
-        T2 = torch.empty_like(Tt)
-        hl.hl_targets(hf, r, hc, None, rows, 1.0, T2)
+        hl.hl_targets(hf, r, hc, None, rows, 1.0, Tt)
         torch.cuda.synchronize()
         corr_ms += e2.elapsed_time(e3)
-        corr += float(T2.pow(2).sum())
-        corr0 += float(T2[:, 0].pow(2).sum())
+        corr += float(Tt.pow(2).sum())
+        corr0 += float(Tt[:, 0].pow(2).sum())
         hl.hl_destroy(hc)
         hl.hl_destroy(hf)
     hl.hl_mlp_destroy(net)

@@ -446,7 +446,7 @@ def test_source_superposition():
     np.testing.assert_allclose(uf, u0 + us, rtol=0, atol=1e-12 * np.abs(uf).max())
 
 
-def test_long_double_build_agrees_with_binary64():
+def test_double_double_build_agrees_with_binary64():
     """The double-double build (the judge of long GPU runs) is the same algorithm: on a short
     run the two builds agree to binary64 rounding, and on the 1000-step 1D workload they
     differ by no more than the binary64 build's accumulated rounding."""
@@ -454,15 +454,15 @@ def test_long_double_build_agrees_with_binary64():
     dt = I.cfl_dt(ncell)
     st = I.random_state(d, m, ncell, seed=31)
     p64, u64 = oracle.run(d, m, ncell, dt, st.p, st.u, 3)
-    pld, uld = oracle.run(d, m, ncell, dt, st.p, st.u, 3, prec="dd")
-    assert np.abs(p64 - pld).max() <= 1e-13 * np.abs(pld).max()
-    assert np.abs(u64 - uld).max() <= 1e-13 * np.abs(uld).max()
+    pdd, udd = oracle.run(d, m, ncell, dt, st.p, st.u, 3, prec="dd")
+    assert np.abs(p64 - pdd).max() <= 1e-13 * np.abs(pdd).max()
+    assert np.abs(u64 - udd).max() <= 1e-13 * np.abs(udd).max()
     d, m, ncell = 1, 3, [64]
     dt = I.cfl_dt(ncell)
     st = I.standing_mode(d, m, ncell, dt, wave=[3])
     p64, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000)
-    pld, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="dd")
-    assert np.abs(p64 - pld).max() <= 1e-11 * np.abs(pld).max()
+    pdd, _ = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec="dd")
+    assert np.abs(p64 - pdd).max() <= 1e-11 * np.abs(pdd).max()
 
 
 # ----------------------------------------------------------------------------- learned correction
