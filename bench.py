@@ -293,6 +293,43 @@ def run_aux(args, rank=0, world=1, dist=None):
             modes[name]["roofline"] = {"bound": "hbm", "achieved": modes[name]["hbm_gbs"], "peak": hbm,
                                        "unit": "GB/s", "frac": modes[name]["hbm_gbs"] / hbm,
                                        "peak_source": "measured" if peaks else "fallback"}
+        if ex is not None:
+            # equal L2 error: plain FP64 on coarser grids to the same final time; each
+            # mode is compared with the coarsest FP64 grid whose error is no larger
+            t_end = lf * dt
+            ladder = []
+            for n2 in (48, 64, 80, 96, 128, 160):
+                c2 = [n2] * d
+                steps2 = int(math.ceil(t_end / I.cfl_dt(c2) - 1e-9))
+                dt2 = t_end / steps2
+                st2 = I.plane_wave(m, c2, dt2, seed=3)
+                ex2 = I.plane_wave(m, c2, dt2, seed=3, t0=t_end)
+                h = hl.hl_create(d, m, c2, dt2)
+                hl.hl_set_stream(h, stream)
+                hl.hl_set_initial(h, st2.p, st2.u)
+                hl.hl_step(h, 2)
+                hl.hl_set_initial(h, st2.p, st2.u)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hl.hl_step(h, steps2)
+                e1.record(stream)
+                hl.hl_sync(h)
+                pg2, _, _, _ = hl.hl_get_fields(h)
+                hl.hl_destroy(h)
+                ladder.append({"n": n2, "steps": steps2, "ms_run": e0.elapsed_time(e1),
+                               "l2_err_p_vs_exact": I.l2_error(d, c2, pg2, ex2.p)})
+            ladder.append({"n": ncell[0], "steps": lf, "ms_run": modes["fp64"]["ms_per_step"] * lf,
+                           "l2_err_p_vs_exact": modes["fp64"]["l2_err_p_vs_exact"]})
+            for name in ("fp32", "fp32_comp"):
+                e = modes[name]["l2_err_p_vs_exact"]
+                ok = [r for r in ladder if r["l2_err_p_vs_exact"] <= e * 1.001]  # equal within 0.1%
+                if ok:
+                    r = min(ok, key=lambda r: r["ms_run"])
+                    t_mode = modes[name]["ms_per_step"] * lf
+                    modes[name]["fp64_at_equal_error"] = {
+                        "n": r["n"], "ms_run": r["ms_run"], "l2_err_p_vs_exact": r["l2_err_p_vs_exact"],
+                        "ms_run_mode": t_mode, "speedup_vs_fp64_at_equal_error": r["ms_run"] / t_mode}
+            out["fp64_error_ladder"] = ladder
         out.update({"workload": args.workload, "value": modes["fp32_comp"]["value"],
                     "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
                     "modes": modes})
@@ -405,13 +442,14 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
     T /= out_scale
     net = hl.hl_mlp_create(7)
     hl.hl_mlp_set_stream(net, stream)
-    g = torch.Generator(device="cpu").manual_seed(0)
     iters, batch = 3000, 8192
+    Xb = torch.empty((batch, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
+    Tb = torch.empty((batch, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for it in range(iters):
-        idx = torch.randint(0, n, (batch,), generator=g).to(dev)
-        hl.hl_mlp_loss_grad(net, X[idx].contiguous(), T[idx].contiguous(), batch, want_loss=False)
+    for it in range(iters):   # stream-ordered: draw, loss and gradient, Adam; no host round trip
+        hl.hl_mlp_sample(net, X, T, batch, 0, it, Xb, Tb)
+        hl.hl_mlp_loss_grad(net, Xb, Tb, batch, want_loss=False)
         hl.hl_mlp_adam_step(net, 1e-3 if it < 2000 else 2e-4)
     e1.record(stream)
     final_loss = hl.hl_mlp_loss_grad(net, X[:65536].contiguous(), T[:65536].contiguous(), min(n, 65536))

@@ -232,11 +232,14 @@ enum {
                                 batched handles, 0 otherwise                  */
     HL_OPT_TILE = 4          /* thread-block tile shape index 0..HL_NUM_TILES-1
                                 (nodes per block along x and y: 128x1, 256x1,
-                                64x2, 32x4, 32x8, 64x4, 16x8, 16x16; dim = 1
-                                folds the tile into x); hl_autotune picks one  */
+                                64x2, 32x4, 32x8, 64x4, 16x8, 16x16, then the
+                                paired shapes 32x4, 32x8, 64x4, 16x16 whose
+                                FP64 kernels give each thread two nodes
+                                adjacent along y; dim = 1 folds the tile into
+                                x and never pairs); hl_autotune picks one     */
 };
 
-#define HL_NUM_TILES 8
+#define HL_NUM_TILES 12
 
 /*
  * hl_set_option -- set an execution option (see the HL_OPT_* values).
@@ -352,6 +355,18 @@ int hl_mlp_forward(hl_mlp *mlp, const float *X_dev, int rows, float *Y_dev);
  * the mean squared error; passing it synchronises the stream.
  */
 int hl_mlp_loss_grad(hl_mlp *mlp, const float *X_dev, const float *T_dev, int rows, double *loss);
+
+/*
+ * hl_mlp_sample -- draw a training minibatch on the device: row i of draw
+ * `step` copies pool row splitmix64(seed + (step*rows + i + 1) * 0x9e3779b97f4a7c15)
+ * mod pool_rows (SplitMix64, Steele, Lea and Flood 2014) from X_pool[pool_rows][288]
+ * (and T_pool[pool_rows][16], may be NULL) into X_dev[rows][288] (and T_dev),
+ * on the network's stream.  The paper has no counterpart: this is training
+ * plumbing for the learned correction, so that a training loop needs no host
+ * round trip.  All buffers are device memory owned by the caller.
+ */
+int hl_mlp_sample(hl_mlp *mlp, const float *X_pool, const float *T_pool, int64_t pool_rows, int rows, uint64_t seed,
+                  uint64_t step, float *X_dev, float *T_dev);
 
 /* hl_mlp_adam_step -- one Adam update (beta1 0.9, beta2 0.999, eps 1e-8) with the current gradient. */
 int hl_mlp_adam_step(hl_mlp *mlp, float lr);

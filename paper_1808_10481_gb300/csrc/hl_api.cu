@@ -422,6 +422,7 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.total_tiles = h->total_tiles;
     a.tx = h->dim == 1 ? kTiles[h->tile][0] * kTiles[h->tile][1] : kTiles[h->tile][0];
     a.ty = h->dim == 1 ? 1 : kTiles[h->tile][1];
+    a.pair = h->dim == 1 ? 0 : kTiles[h->tile][2];
     a.P = P;
     a.U = U;
     a.nsteps = n_steps;

@@ -45,6 +45,9 @@ struct Shape {
     static constexpr bool kParam = NCOEF * 8 <= 28 * 1024;
     // the u-half keeps all dim output blocks live only when they fit in registers
     static constexpr bool kUFused = D * NQ <= 96;
+    // paired kernels (two nodes per thread) while both nodes' outputs fit
+    static constexpr bool kPairP = D >= 2 && 2 * NQ <= 64;
+    static constexpr bool kPairU = D >= 2 && 2 * D * NQ <= 64;
 };
 
 __host__ __device__ constexpr bool coef_nonzero(int D, int n, int i, int s, int l)
@@ -95,11 +98,17 @@ struct GridDesc {
 
 // In-place Walsh-Hadamard butterfly over the 2^D vertex values:
 // afterwards x[pat] = sum_v prod_{k: v_k=1} (bit k of pat ? -1 : +1) x_v.
+// The levels run in the order x, z, y: with y last, the paired kernels (two
+// nodes adjacent along y) share every level but the last and stay bitwise
+// identical to the one-node kernels.
 template <int D>
 __device__ __forceinline__ void butterfly(double *x)
 {
+    constexpr int order[3] = {0, 2, 1};
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
+    for (int o = 0; o < 3; ++o) {
+        const int k = order[o];
+        if (k >= D) continue;
 #pragma unroll
         for (int v = 0; v < (1 << D); ++v) {
             if (!(v & (1 << k))) {
@@ -142,6 +151,13 @@ __device__ __forceinline__ void vertex_nodes(const GridDesc &g, int64_t node, in
         }
         vtx[v] = idx;
     }
+}
+
+// Inf/NaN test on the exponent bits: integer pipe only (a floating-point
+// compare would take a slot of the FP64 pipe, the kernels' bottleneck)
+__device__ __forceinline__ bool nonfinite(double v)
+{
+    return ((unsigned)__double2hiint(v) & 0x7FF00000u) == 0x7FF00000u;
 }
 
 __device__ __forceinline__ void report_nonfinite(bool bad, unsigned *status)
@@ -244,20 +260,26 @@ struct CoefShots {
     }
 };
 
-// Locate this block's shot and node; false if the thread is outside the grid.
-template <int D>
-__device__ __forceinline__ bool tile_node(const ShotDesc *__restrict__ shots, int n_shots, int &shot, ShotDesc &sd,
-                                          int64_t &node)
+// The shot of this block: the last shot whose first tile is <= blockIdx.x.
+__device__ __forceinline__ void find_shot(const ShotDesc *__restrict__ shots, int n_shots, int &shot, ShotDesc &sd)
 {
     const int tile = blockIdx.x;
     int lo = 0, hi = n_shots - 1;
-    while (lo < hi) {  // last shot with tile_begin <= tile
+    while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (shots[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
     shot = lo;
     sd = shots[lo];
-    int t = tile - sd.tile_begin;
+}
+
+// Locate this block's shot and node; false if the thread is outside the grid.
+template <int D>
+__device__ __forceinline__ bool tile_node(const ShotDesc *__restrict__ shots, int n_shots, int &shot, ShotDesc &sd,
+                                          int64_t &node)
+{
+    find_shot(shots, n_shots, shot, sd);
+    int t = blockIdx.x - sd.tile_begin;
     const int tx = t % sd.tiles[0];
     t /= sd.tiles[0];
     const int ty = t % sd.tiles[1];
@@ -294,7 +316,7 @@ __global__ void __launch_bounds__(256) k_p_half(const double *__restrict__ U, do
     for (int s = 0; s < S::NQ; ++s) {
         const double v = Ps[(int64_t)s * g.nnode + node] + out[s];
         Ps[(int64_t)s * g.nnode + node] = v;
-        bad |= !isfinite(v);
+        bad |= nonfinite(v);
     }
     report_nonfinite(bad, status);
 }
@@ -327,8 +349,192 @@ __global__ void __launch_bounds__(256) k_u_half(const double *__restrict__ P, do
             double *dst = Us + (int64_t)((I0 + ii) * S::NQ + s) * g.nnode + node;
             const double v = *dst + out[ii * S::NQ + s];
             *dst = v;
-            bad |= !isfinite(v);
+            bad |= nonfinite(v);
         }
+    report_nonfinite(bad, status);
+}
+
+// ---------------------------------------------------------------------------
+// Paired grid kernels: one thread owns two nodes adjacent along y, rows iy and
+// iy+1 of a tile whose height is 2*blockDim.y (the tile table is the same as
+// for the one-node kernels).  The two cells share one y-row of vertices, whose
+// butterfly levels along x (and z) are computed once for both nodes: per slot
+// 3 rows instead of 4 are loaded and reduced.
+template <int D>
+struct Pair {
+    static constexpr int NW = 1 << (D - 1);  // vertices of one y-row: bit 0 = x, bit 1 = z
+};
+
+__device__ __forceinline__ int wrap_index(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Returns how many of the thread's two nodes lie inside the grid (0, 1 or 2).
+template <int D>
+__device__ __forceinline__ int tile_pair(const ShotDesc *__restrict__ shots, int n_shots, int &shot, ShotDesc &sd,
+                                         int &ix, int &iy, int &iz)
+{
+    find_shot(shots, n_shots, shot, sd);
+    int t = blockIdx.x - sd.tile_begin;
+    const int tx = t % sd.tiles[0];
+    t /= sd.tiles[0];
+    const int ty = t % sd.tiles[1];
+    iz = t / sd.tiles[1];
+    ix = tx * blockDim.x + threadIdx.x;
+    iy = ty * (2 * blockDim.y) + 2 * threadIdx.y;
+    if (ix >= sd.n[0] || iy >= sd.n[1] || iz >= sd.n[2]) return 0;
+    return iy + 1 < sd.n[1] ? 2 : 1;
+}
+
+// vertex nodes of the three y-rows iy+lo, iy+lo+1, iy+lo+2 (periodic); node A
+// uses rows 0 and 1, node B rows 1 and 2
+template <int D>
+__device__ __forceinline__ void pair_vertices(const ShotDesc &sd, int ix, int iy, int iz, int lo,
+                                              int (&vtx)[3][Pair<D>::NW])
+{
+    const int xs[2] = {wrap_index(ix + lo, sd.n[0]), wrap_index(ix + lo + 1, sd.n[0])};
+    int zs[2] = {0, 0};
+    if constexpr (D == 3) {
+        zs[0] = wrap_index(iz + lo, sd.n[2]);
+        zs[1] = wrap_index(iz + lo + 1, sd.n[2]);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int y = wrap_index(iy + lo + r, sd.n[1]);
+#pragma unroll
+        for (int w = 0; w < Pair<D>::NW; ++w) vtx[r][w] = xs[w & 1] + sd.n[0] * (y + sd.n[1] * zs[(w >> 1) & 1]);
+    }
+}
+
+// butterflies of both cells for one (component, slot): levels x (and z) per
+// row, then the y level over rows (0,1) for A and (1,2) for B
+template <int D, class Ld>
+__device__ __forceinline__ void pair_butterfly(const Ld &ld, int comp, int slot, const int (&vtx)[3][Pair<D>::NW],
+                                               double *xa, double *xb)
+{
+    constexpr int NW = Pair<D>::NW;
+    double r[3][NW];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) r[k][w] = ld(comp, slot, vtx[k][w]);
+        butterfly<D - 1>(r[k]);
+    }
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int p0 = (w & 1) | ((w >> 1) << 2);  // row pattern -> cell pattern (y bit = 2)
+        xa[p0] = r[0][w] + r[1][w];
+        xa[p0 | 2] = r[0][w] - r[1][w];
+        xb[p0] = r[1][w] + r[2][w];
+        xb[p0 | 2] = r[1][w] - r[2][w];
+    }
+}
+
+template <int D, int M, class CP>
+__global__ void __launch_bounds__(256) k_p_half_pair(const double *__restrict__ U, double *__restrict__ P,
+                                                     const ShotDesc *__restrict__ shots, int n_shots, CP cp,
+                                                     unsigned *status)
+{
+    using S = Shape<D, M>;
+    int shot, ix, iy, iz;
+    ShotDesc sd;
+    const int nodes = tile_pair<D>(shots, n_shots, shot, sd, ix, iy, iz);
+    if (!nodes) return;
+    int vtx[3][Pair<D>::NW];
+    pair_vertices<D>(sd, ix, iy, iz, -1, vtx);
+    const auto &coef = cp.at(shot);
+    const GlobalLd ld{U + sd.u_off, sd.nnode, S::NQ};
+    double oa[S::NQ], ob[S::NQ];
+#pragma unroll
+    for (int s = 0; s < S::NQ; ++s) oa[s] = ob[s] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int l = 0; l < S::NQ; ++l) {
+            double xa[S::NV], xb[S::NV];
+            pair_butterfly<D>(ld, i, l, vtx, xa, xb);
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) {
+                if (coef_nonzero(D, S::n, i, s, l)) {
+                    const double c = coef.get(coef_index(S::NQ, i, l, s));
+                    const int pat = bfly_pattern(D, S::n, i, s, l);
+                    oa[s] = fma(c, xa[pat], oa[s]);
+                    ob[s] = fma(c, xb[pat], ob[s]);
+                }
+            }
+        }
+    }
+    double *Ps = P + sd.p_off;
+    const int64_t na = ix + (int64_t)sd.n[0] * (iy + (int64_t)sd.n[1] * iz);
+    bool bad = false;
+#pragma unroll
+    for (int s = 0; s < S::NQ; ++s) {
+        const double v = Ps[(int64_t)s * sd.nnode + na] + oa[s];
+        Ps[(int64_t)s * sd.nnode + na] = v;
+        bad |= nonfinite(v);
+    }
+    if (nodes == 2) {
+        const int64_t nb = na + sd.n[0];
+#pragma unroll
+        for (int s = 0; s < S::NQ; ++s) {
+            const double v = Ps[(int64_t)s * sd.nnode + nb] + ob[s];
+            Ps[(int64_t)s * sd.nnode + nb] = v;
+            bad |= nonfinite(v);
+        }
+    }
+    report_nonfinite(bad, status);
+}
+
+template <int D, int M, class CP>
+__global__ void __launch_bounds__(256) k_u_half_pair(const double *__restrict__ P, double *__restrict__ U,
+                                                     const ShotDesc *__restrict__ shots, int n_shots, CP cp,
+                                                     unsigned *status)
+{
+    using S = Shape<D, M>;
+    constexpr int NO = D * S::NQ;
+    int shot, ix, iy, iz;
+    ShotDesc sd;
+    const int nodes = tile_pair<D>(shots, n_shots, shot, sd, ix, iy, iz);
+    if (!nodes) return;
+    int vtx[3][Pair<D>::NW];
+    pair_vertices<D>(sd, ix, iy, iz, 0, vtx);
+    const auto &coef = cp.at(shot);
+    const GlobalLd ld{P + sd.p_off, sd.nnode, S::NQ};
+    double oa[NO], ob[NO];
+#pragma unroll
+    for (int e = 0; e < NO; ++e) oa[e] = ob[e] = 0.0;
+#pragma unroll
+    for (int l = 0; l < S::NQ; ++l) {
+        double xa[S::NV], xb[S::NV];
+        pair_butterfly<D>(ld, 0, l, vtx, xa, xb);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int s = 0; s < S::NQ; ++s) {
+                if (coef_nonzero(D, S::n, i, s, l)) {
+                    const double c = coef.get(coef_index(S::NQ, i, l, s));
+                    const int pat = bfly_pattern(D, S::n, i, s, l);
+                    oa[i * S::NQ + s] = fma(c, xa[pat], oa[i * S::NQ + s]);
+                    ob[i * S::NQ + s] = fma(c, xb[pat], ob[i * S::NQ + s]);
+                }
+            }
+    }
+    double *Us = U + sd.u_off;
+    const int64_t na = ix + (int64_t)sd.n[0] * (iy + (int64_t)sd.n[1] * iz);
+    bool bad = false;
+#pragma unroll
+    for (int e = 0; e < NO; ++e) {
+        const double v = Us[(int64_t)e * sd.nnode + na] + oa[e];
+        Us[(int64_t)e * sd.nnode + na] = v;
+        bad |= nonfinite(v);
+    }
+    if (nodes == 2) {
+        const int64_t nb = na + sd.n[0];
+#pragma unroll
+        for (int e = 0; e < NO; ++e) {
+            const double v = Us[(int64_t)e * sd.nnode + nb] + ob[e];
+            Us[(int64_t)e * sd.nnode + nb] = v;
+            bad |= nonfinite(v);
+        }
+    }
     report_nonfinite(bad, status);
 }
 
@@ -347,7 +553,7 @@ __device__ __forceinline__ void small_u_split(const C &coef, const Ld &ld, const
         for (int s = 0; s < S::NQ; ++s) {
             const double v = sU[(I * S::NQ + s) * nn + node] + out[s];
             sU[(I * S::NQ + s) * nn + node] = v;
-            bad |= !isfinite(v);
+            bad |= nonfinite(v);
         }
         small_u_split<D, M, I + 1>(coef, ld, vtx, sU, nn, node, bad);
     }
@@ -383,7 +589,7 @@ __global__ void __launch_bounds__(256) k_small(double *__restrict__ P, double *_
             for (int s = 0; s < S::NQ; ++s) {
                 const double v = sP[s * nn + node] + out[s];
                 sP[s * nn + node] = v;
-                bad |= !isfinite(v);
+                bad |= nonfinite(v);
             }
         }
         __syncthreads();
@@ -399,7 +605,7 @@ __global__ void __launch_bounds__(256) k_small(double *__restrict__ P, double *_
                 for (int e = 0; e < D * S::NQ; ++e) {
                     const double v = sU[e * nn + node] + out[e];
                     sU[e * nn + node] = v;
-                    bad |= !isfinite(v);
+                    bad |= nonfinite(v);
                 }
             } else {
                 small_u_split<D, M, 0>(coef, ldP, vtx, sU, nn, node, bad);

@@ -36,18 +36,37 @@ static cudaError_t run_grid(const LaunchFp64 &a, const CP &cp)
 {
     using S = Shape<D, M>;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
+    // paired tiles (even height) run two nodes per thread along y
+    const bool pair = D >= 2 && a.pair && a.ty % 2 == 0;
+    const dim3 pblock((unsigned)a.tx, (unsigned)(a.ty / 2));
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        k_p_half<D, M, CP><<<grid, block, 0, a.stream>>>(a.U, a.P, a.shots, a.n_shots, cp, a.status);
+        bool done = false;
+        if constexpr (S::kPairP) {
+            if (pair) {
+                k_p_half_pair<D, M, CP><<<grid, pblock, 0, a.stream>>>(a.U, a.P, a.shots, a.n_shots, cp, a.status);
+                done = true;
+            }
+        }
+        if (!done) k_p_half<D, M, CP><<<grid, block, 0, a.stream>>>(a.U, a.P, a.shots, a.n_shots, cp, a.status);
         if (a.src && a.src->active) {
             cudaError_t e = launch_source(*a.src, a.shots, a.P, S::NQ, a.step0 + st, a.stream);
             if (e != cudaSuccess) return e;
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
-        if constexpr (S::kUFused)
-            k_u_half<D, M, 0, D, CP><<<grid, block, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cp, a.status);
-        else
-            launch_u_split<D, M, 0, CP>(a, cp, grid, block);
+        done = false;
+        if constexpr (S::kPairU) {
+            if (pair) {
+                k_u_half_pair<D, M, CP><<<grid, pblock, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cp, a.status);
+                done = true;
+            }
+        }
+        if (!done) {
+            if constexpr (S::kUFused)
+                k_u_half<D, M, 0, D, CP><<<grid, block, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cp, a.status);
+            else
+                launch_u_split<D, M, 0, CP>(a, cp, grid, block);
+        }
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();

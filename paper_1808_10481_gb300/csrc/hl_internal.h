@@ -59,7 +59,8 @@ struct LaunchFp64 {
     const ShotDesc *shots;    // device shot table
     int n_shots;
     int total_tiles;
-    int tx, ty;               // tile (block) shape
+    int tx, ty;               // tile shape (nodes per tile along x, y)
+    int pair = 0;             // 1: FP64 kernels take two nodes per thread along y
     double *P;                // p blocks [q][node] of every shot
     double *U;                // u blocks [comp][q][node] of every shot
     int64_t nsteps;

@@ -35,9 +35,11 @@ constexpr int kIn = HL_MLP_IN, kH = HL_MLP_HIDDEN, kOut = HL_MLP_OUT;
 // ---------------------------------------------------------------------------
 // C[M x N] = A[M x K] B[K x N] (+ bias[n]) (relu) ; element (r, c) of a matrix X
 // is X.p[r * X.rs + c * X.cs], so transposes are free.  64x64 block tile,
-// 4 warps of 32x32, K staged 32 at a time through shared memory as BF16 (A as
-// [m][k], B transposed as [n][k], so every fragment register is one 32-bit
-// shared load).  Global loads run along whichever index is contiguous.
+// 4 warps of 32x32, K in steps of 32.  Both operands are kept in shared memory
+// as BF16 with k innermost (A as [m][k], B as [n][k]), so every fragment
+// register is one 32-bit shared load.  The next k-step is loaded from global
+// memory into registers (float4 along whichever index is contiguous) while the
+// current one is multiplied, then converted and stored to the other buffer.
 // Split-K: block z covers K range [z*kc, (z+1)*kc) and writes its partial sums
 // to part[z]; k_gemm_reduce adds them in a fixed order (deterministic).
 struct Mat {
@@ -46,24 +48,105 @@ struct Mat {
 };
 
 constexpr int BM = 64, BN = 64, BK = 32, PADK = 8;
+constexpr int LDS = BK + PADK;  // shared row length (bf16): 80 bytes
 
 __device__ __forceinline__ uint32_t lds_pair(const __nv_bfloat16 *p)
 {
     return *reinterpret_cast<const uint32_t *>(p);
 }
 
-__global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ C, int64_t ldc, int M, int N, int K,
-                                              int kc, const float *__restrict__ bias, int relu,
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// One 64 (outer) x 32 (k) operand tile of the view V(o, k) = p[o*so + k*sk],
+// valid for o < olim and k < klim.  Mode 1: k contiguous, mode 2: o
+// contiguous (both float4), mode 0: scalar.  16 values per thread.
+struct TileLd {
+    const float *p;
+    int64_t so, sk;
+    int olim;
+    int mode;
+    float v[16];
+
+    __device__ __forceinline__ void load(int o0, int k0, int klim, int tid)
+    {
+        if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int idx = tid + i * 128, o = idx >> 3, k = (idx & 7) * 4;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (o0 + o < olim && k0 + k < klim)
+                    x = __ldg(reinterpret_cast<const float4 *>(p + (int64_t)(o0 + o) * so + (k0 + k)));
+                v[4 * i] = x.x, v[4 * i + 1] = x.y, v[4 * i + 2] = x.z, v[4 * i + 3] = x.w;
+            }
+        } else if (mode == 2) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int idx = tid + i * 128, k = idx >> 4, o = (idx & 15) * 4;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (o0 + o < olim && k0 + k < klim)
+                    x = __ldg(reinterpret_cast<const float4 *>(p + (o0 + o) + (int64_t)(k0 + k) * sk));
+                v[4 * i] = x.x, v[4 * i + 1] = x.y, v[4 * i + 2] = x.z, v[4 * i + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int idx = tid + i * 128, o = idx >> 5, k = idx & 31;
+                v[i] = (o0 + o < olim && k0 + k < klim) ? p[(int64_t)(o0 + o) * so + (int64_t)(k0 + k) * sk] : 0.f;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void store(__nv_bfloat16 (*dst)[LDS], int tid) const
+    {
+        if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int idx = tid + i * 128, o = idx >> 3, k = (idx & 7) * 4;
+                *reinterpret_cast<uint2 *>(&dst[o][k]) = make_uint2(pack2(v[4 * i], v[4 * i + 1]),
+                                                                    pack2(v[4 * i + 2], v[4 * i + 3]));
+            }
+        } else if (mode == 2) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int idx = tid + i * 128, k = idx >> 4, o = (idx & 15) * 4;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dst[o + j][k] = __float2bfloat16_rn(v[4 * i + j]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int idx = tid + i * 128;
+                dst[idx >> 5][idx & 31] = __float2bfloat16_rn(v[i]);
+            }
+        }
+    }
+};
+
+// float4 paths need 16-byte aligned rows along the contiguous index and
+// extents that are multiples of 4 there
+__host__ __forceinline__ int tile_mode(const float *p, int64_t so, int64_t sk, int olim, int K)
+{
+    const bool al = ((uintptr_t)p & 15) == 0;
+    if (al && sk == 1 && so % 4 == 0 && K % 4 == 0) return 1;
+    if (al && so == 1 && sk % 4 == 0 && olim % 4 == 0) return 2;
+    return 0;
+}
+
+__global__ void __launch_bounds__(128, 4) k_gemm(TileLd ta, TileLd tb, float *__restrict__ C, int64_t ldc, int M,
+                                              int N, int K, int kc, const float *__restrict__ bias, int relu,
                                               float *__restrict__ part)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PADK];
-    __shared__ __align__(16) __nv_bfloat16 Bt[BN][BK + PADK];
+    __shared__ __align__(16) __nv_bfloat16 As[2][BM][LDS];
+    __shared__ __align__(16) __nv_bfloat16 Bt[2][BN][LDS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kbeg = blockIdx.z * kc, kend = min(K, kbeg + kc);
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const bool a_kfast = A.cs == 1, b_nfast = B.cs == 1;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -71,36 +154,36 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    int cur = 0;
+    if (kbeg < kend) {
+        ta.load(m0, kbeg, kend, tid);
+        tb.load(n0, kbeg, kend, tid);
+        ta.store(As[0], tid);
+        tb.store(Bt[0], tid);
+    }
+    __syncthreads();
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += 128) {
-            const int r = a_kfast ? e / BK : e % BM, c = a_kfast ? e % BK : e / BM;
-            const int gr = m0 + r, gc = k0 + c;
-            const float v = (gr < M && gc < kend) ? A.p[(int64_t)gr * A.rs + (int64_t)gc * A.cs] : 0.f;
-            As[r][c] = __float2bfloat16_rn(v);
+        const bool next = k0 + BK < kend;
+        if (next) {  // in flight while this step is multiplied
+            ta.load(m0, k0 + BK, kend, tid);
+            tb.load(n0, k0 + BK, kend, tid);
         }
-        for (int e = tid; e < BK * BN; e += 128) {
-            const int r = b_nfast ? e / BN : e % BK, c = b_nfast ? e % BN : e / BK;
-            const int gr = k0 + r, gc = n0 + c;
-            const float v = (gr < kend && gc < N) ? B.p[(int64_t)gr * B.rs + (int64_t)gc * B.cs] : 0.f;
-            Bt[c][r] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t af[2][4], bf[4][2];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int r = wm + i * 16 + g;
-                af[i][0] = lds_pair(&As[r][kk + 2 * t]);
-                af[i][1] = lds_pair(&As[r + 8][kk + 2 * t]);
-                af[i][2] = lds_pair(&As[r][kk + 2 * t + 8]);
-                af[i][3] = lds_pair(&As[r + 8][kk + 2 * t + 8]);
+                af[i][0] = lds_pair(&As[cur][r][kk + 2 * t]);
+                af[i][1] = lds_pair(&As[cur][r + 8][kk + 2 * t]);
+                af[i][2] = lds_pair(&As[cur][r][kk + 2 * t + 8]);
+                af[i][3] = lds_pair(&As[cur][r + 8][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = wn + j * 8 + g;
-                bf[j][0] = lds_pair(&Bt[c][kk + 2 * t]);
-                bf[j][1] = lds_pair(&Bt[c][kk + 2 * t + 8]);
+                bf[j][0] = lds_pair(&Bt[cur][c][kk + 2 * t]);
+                bf[j][1] = lds_pair(&Bt[cur][c][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -112,7 +195,12 @@ __global__ void __launch_bounds__(128) k_gemm(Mat A, Mat B, float *__restrict__ 
                         : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
                         : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bf[j][0]), "r"(bf[j][1]));
         }
+        if (next) {  // the other buffer's readers finished at the previous barrier
+            ta.store(As[cur ^ 1], tid);
+            tb.store(Bt[cur ^ 1], tid);
+        }
         __syncthreads();
+        cur ^= 1;
     }
     float *out = part ? part + (int64_t)blockIdx.z * M * N : C;
     const int64_t ld = part ? N : ldc;
@@ -161,7 +249,11 @@ static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K
         splits *= 2;
     const int kc = ((K + splits - 1) / splits + BK - 1) / BK * BK;
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)splits);
-    k_gemm<<<grid, 128, 0, st>>>(A, B, C, ldc, M, N, K, kc, bias, relu, splits > 1 ? work : nullptr);
+    // operand views with k as the second index: A(m, k), and B as B(n, k)
+    TileLd ta{A.p, A.rs, A.cs, M, tile_mode(A.p, A.rs, A.cs, M, K), {}};
+    TileLd tb{B.p, B.cs, B.rs, N, tile_mode(B.p, B.cs, B.rs, N, K), {}};
+    // split boundaries stay multiples of BK, so the float4 k-ranges never straddle them
+    k_gemm<<<grid, 128, 0, st>>>(ta, tb, C, ldc, M, N, K, kc, bias, relu, splits > 1 ? work : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     const int64_t n = (int64_t)M * N;
@@ -527,6 +619,41 @@ extern "C" int hl_mlp_adam_step(hl_mlp *h, float lr)
     const float c1 = 1.f - std::pow(b1, (float)h->adam_t), c2 = 1.f - std::pow(b2, (float)h->adam_t);
     k_adam<<<blocks_for(N_PARAMS, 256), 256, 0, h->stream>>>(h->w, h->g, h->m1, h->m2, N_PARAMS, lr, b1, b2, 1e-8f,
                                                             c1, c2);
+    MLP_CK(h, cudaGetLastError());
+    return HL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Minibatch draw on the device: row i of step `step` takes pool row
+// splitmix64(seed + (step * rows + i) * golden) mod pool_rows, with SplitMix64
+// the counter-based generator of Steele, Lea and Flood (OOPSLA 2014): add the
+// golden-ratio increment, then the xor-shift / multiply finaliser.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_sample(const float *__restrict__ Xp, const float *__restrict__ Tp, int64_t pool_rows, int rows,
+                         uint64_t seed, uint64_t step, float *__restrict__ X, float *__restrict__ T)
+{
+    const int r = blockIdx.x;
+    const uint64_t ctr = step * (uint64_t)rows + (uint64_t)r;
+    const int64_t src = (int64_t)(splitmix64(seed + (ctr + 1) * 0x9e3779b97f4a7c15ull) % (uint64_t)pool_rows);
+    for (int c = threadIdx.x; c < kIn; c += blockDim.x) X[(int64_t)r * kIn + c] = Xp[src * kIn + c];
+    if (Tp)
+        for (int c = threadIdx.x; c < kOut; c += blockDim.x) T[(int64_t)r * kOut + c] = Tp[src * kOut + c];
+}
+
+extern "C" int hl_mlp_sample(hl_mlp *h, const float *X_pool, const float *T_pool, int64_t pool_rows, int rows,
+                             uint64_t seed, uint64_t step, float *X_dev, float *T_dev)
+{
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    if (!X_pool || !X_dev || pool_rows < 1 || rows < 1 || (T_pool && !T_dev))
+        return mlp_err(h, HL_EINVAL, "bad sample arguments");
+    k_sample<<<rows, 96, 0, h->stream>>>(X_pool, T_pool, pool_rows, rows, seed, step, X_dev, T_dev);
     MLP_CK(h, cudaGetLastError());
     return HL_OK;
 }

@@ -13,7 +13,10 @@
 namespace hl {
 
 // tile (thread block) shapes the autotuner chooses from: (TX, TY)
-constexpr int kTiles[][2] = {{128, 1}, {256, 1}, {64, 2}, {32, 4}, {32, 8}, {64, 4}, {16, 8}, {16, 16}};
+// {nodes per tile along x, along y, paired}: paired tiles run the FP64
+// kernels with two nodes per thread along y (blocks of x * y/2 threads)
+constexpr int kTiles[][3] = {{128, 1, 0}, {256, 1, 0}, {64, 2, 0}, {32, 4, 0}, {32, 8, 0}, {64, 4, 0},
+                             {16, 8, 0},  {16, 16, 0}, {32, 4, 1}, {32, 8, 1}, {64, 4, 1}, {16, 16, 1}};
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
 static_assert(kNumTiles == HL_NUM_TILES, "tile table and header disagree");
 

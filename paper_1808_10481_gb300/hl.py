@@ -24,9 +24,10 @@ HL_OPT_KERNEL_PATH = 1
 HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
-HL_NUM_TILES = 8
+HL_NUM_TILES = 12
 HL_MLP_IN, HL_MLP_HIDDEN, HL_MLP_OUT, HL_MLP_NPARAMS = 288, 128, 16, 55568
-TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16)]
+TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16),
+         (32, 4, "paired"), (32, 8, "paired"), (64, 4, "paired"), (16, 16, "paired")]
 CODE_NAMES = {0: "HL_OK", -1: "HL_EINVAL", -2: "HL_ENOMEM", -3: "HL_ECUDA", -4: "HL_ETIMEOUT",
               -5: "HL_ENONFINITE", -6: "HL_ESTATE"}
 
@@ -73,6 +74,7 @@ _SIGNATURES = [
     ("hl_mlp_forward", ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     ("hl_mlp_loss_grad", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(_D)]),
     ("hl_mlp_adam_step", ctypes.c_int, [_P, ctypes.c_float]),
+    ("hl_mlp_sample", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _P, _P]),
     ("hl_features", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
     ("hl_targets", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _D, _P]),
     ("hl_apply_correction", ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _D]),
@@ -404,6 +406,15 @@ def hl_mlp_loss_grad(m: MLP, X, T, rows: int, want_loss: bool = True):
 
 def hl_mlp_adam_step(m: MLP, lr: float) -> None:
     _mcheck(m, load().hl_mlp_adam_step(m.ptr, ctypes.c_float(lr)))
+
+
+def hl_mlp_sample(m: MLP, X_pool, T_pool, rows: int, seed: int, step: int, X, T=None) -> None:
+    """Device minibatch draw: X[i] = X_pool[splitmix64 index], likewise T."""
+    pool = int(X_pool.shape[0])
+    _mcheck(m, load().hl_mlp_sample(m.ptr, _fptr(X_pool, pool * HL_MLP_IN),
+                                    None if T_pool is None else _fptr(T_pool, pool * HL_MLP_OUT), pool, int(rows),
+                                    int(seed) & (2**64 - 1), int(step) & (2**64 - 1), _fptr(X, rows * HL_MLP_IN),
+                                    None if T is None else _fptr(T, rows * HL_MLP_OUT)))
 
 
 def hl_features(coarse: Handle, nodes, rows: int, feat_scale: float, t_feature: float, X) -> None:

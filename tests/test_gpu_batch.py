@@ -41,6 +41,7 @@ def _run_single(d, m, ncell, dt, p, u, steps, src=None, tile=None):
     try:
         if tile is not None:
             hl.hl_set_option(h, hl.HL_OPT_TILE, tile)
+            hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, 2)
         hl.hl_set_initial(h, p, u)
         if src:
             hl.hl_set_source(h, src["x0"], src["sigma"], src["f0"], src["amp"])
@@ -123,15 +124,17 @@ def test_ricker_batch_from_rest_matches_oracle():
         assert rel_err(pb, po) <= 1e-12 and rel_err(ub, uo) <= 1e-12
 
 
-def test_tile_shape_does_not_change_results():
-    d, m, ncell = 2, 3, [45, 38]
+@pytest.mark.parametrize("d,m,ncell", [(2, 3, [45, 37]), (2, 4, [21, 19]), (3, 2, [13, 11, 7]), (3, 1, [9, 7, 5])])
+def test_tile_shape_does_not_change_results(d, m, ncell):
+    """Every tile shape, paired (two nodes per thread along y, odd row counts leave
+    a lone last row) or not, gives bitwise the same result."""
     dt = I.cfl_dt(ncell)
     st = I.random_state(d, m, ncell, seed=12)
     ref = _run_single(d, m, ncell, dt, st.p, st.u, 6, tile=0)
     for t in range(1, hl.HL_NUM_TILES):
         got = _run_single(d, m, ncell, dt, st.p, st.u, 6, tile=t)
-        np.testing.assert_array_equal(got[0], ref[0])
-        np.testing.assert_array_equal(got[1], ref[1])
+        np.testing.assert_array_equal(got[0], ref[0], err_msg=f"tile {hl.TILES[t]}")
+        np.testing.assert_array_equal(got[1], ref[1], err_msg=f"tile {hl.TILES[t]}")
 
 
 def test_autotune_picks_a_tile_and_leaves_state_untouched():

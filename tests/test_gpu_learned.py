@@ -112,6 +112,30 @@ def _solver(ncell, st, steps):
     return h
 
 
+def _splitmix64_nth(seed, n):
+    """n-th output (n >= 1) of SplitMix64 seeded with `seed` (Steele, Lea and Flood 2014)."""
+    mask = (1 << 64) - 1
+    z = (seed + n * 0x9E3779B97F4A7C15) & mask
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    return z ^ (z >> 31)
+
+
+def test_device_minibatch_draw_follows_splitmix64(net):
+    pool, rows, seed = 1000, 64, 12345
+    rng = np.random.default_rng(8)
+    Xp = torch.from_numpy(rng.standard_normal((pool, M.N_IN)).astype(np.float32)).to(DEV)
+    Tp = torch.from_numpy(rng.standard_normal((pool, M.N_OUT)).astype(np.float32)).to(DEV)
+    X = torch.empty((rows, M.N_IN), dtype=torch.float32, device=DEV)
+    T = torch.empty((rows, M.N_OUT), dtype=torch.float32, device=DEV)
+    for step in (0, 1, 77):
+        hl.hl_mlp_sample(net, Xp, Tp, rows, seed, step, X, T)
+        torch.cuda.synchronize()
+        idx = [_splitmix64_nth(seed, step * rows + i + 1) % pool for i in range(rows)]
+        assert torch.equal(X.cpu(), Xp.cpu()[idx])
+        assert torch.equal(T.cpu(), Tp.cpu()[idx])
+
+
 def test_features_and_targets_match_oracle():
     nc, r = [20, 12], 4
     nf = [nc[0] * r, nc[1] * r]

@@ -64,9 +64,16 @@ def rel_err(got, ref):
     return float(np.abs(np.asarray(got) - np.asarray(ref)).max()) / (scale if scale > 0 else 1.0)
 
 
+PAIRED_TILE = 9   # 32 x 8 nodes, two nodes per thread along y
+
+
 def gpu_run(d, m, ncell, dt, p, u, steps, path=0):
+    """path 0 automatic, 1 single CTA, 2 grid launches, 3 grid launches on a paired tile."""
     h = hl.hl_create(d, m, ncell, dt)
     try:
+        if path == 3:
+            hl.hl_set_option(h, hl.HL_OPT_TILE, PAIRED_TILE)
+            path = 2
         if path:
             hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, path)
         hl.hl_set_initial(h, np.ascontiguousarray(p), np.ascontiguousarray(u))
@@ -87,11 +94,12 @@ SMALL_CASES = (
 )
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 @pytest.mark.parametrize("d,m,ncell", SMALL_CASES)
 def test_random_state_parity(d, m, ncell, path):
-    """Random node data (every slot exercised), both kernel paths, tiny and odd grids
-    where periodic neighbours alias (n = 2, 3)."""
+    """Random node data (every slot exercised), every kernel path (single CTA, one node
+    per thread, two nodes per thread), tiny and odd grids where periodic neighbours
+    alias (n = 2, 3)."""
     if path == 1 and (d + 1) * (m + 1) ** d * int(np.prod(ncell)) * 8 > 200 * 1024:
         pytest.skip("state does not fit the single-CTA path")
     dt = I.cfl_dt(ncell, 0.9)
