@@ -49,8 +49,10 @@ FP64_PEAK_FLOPS = N_SM * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9
 # DRAM traffic of the dominant kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (keyed by the hash of the kernel header).
-TRAFFIC_SOURCE_HASH = None
-TRAFFIC_BYTES = {"p_half": None, "u_half": None}
+# Captured on this workload (512^2, paired 32x8 tile), mean of two launches,
+# ncu's default cache flush before each launch (profiles/traffic_k_p_half_pair_2d_m3_512.md).
+TRAFFIC_SOURCE_HASH = "14b95549c8d41e93"
+TRAFFIC_BYTES = {"p_half": 103940096, "u_half": None}
 
 WORKLOAD = ("2D acoustics p_t+div u=0, u_t+grad p=0, periodic unit square, 512x512 nodes per grid, "
             "m=3 (16 scaled derivatives per node per field), FP64, seeded Gaussian pressure pulse "
