@@ -232,14 +232,16 @@ enum {
                                 batched handles, 0 otherwise                  */
     HL_OPT_TILE = 4          /* thread-block tile shape index 0..HL_NUM_TILES-1
                                 (nodes per block along x and y: 128x1, 256x1,
-                                64x2, 32x4, 32x8, 64x4, 16x8, 16x16, then the
+                                64x2, 32x4, 32x8, 64x4, 16x8, 16x16; then the
                                 paired shapes 32x4, 32x8, 64x4, 16x16 whose
                                 FP64 kernels give each thread two nodes
-                                adjacent along y; dim = 1 folds the tile into
-                                x and never pairs); hl_autotune picks one     */
+                                adjacent along y in both half-steps, and
+                                32x8, 64x4 paired in the p-half only; dim = 1
+                                folds the tile into x and never pairs);
+                                hl_autotune picks one                          */
 };
 
-#define HL_NUM_TILES 12
+#define HL_NUM_TILES 14
 
 /*
  * hl_set_option -- set an execution option (see the HL_OPT_* values).

@@ -36,14 +36,16 @@ static cudaError_t run_grid(const LaunchFp64 &a, const CP &cp)
 {
     using S = Shape<D, M>;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
-    // paired tiles (even height) run two nodes per thread along y
-    const bool pair = D >= 2 && a.pair && a.ty % 2 == 0;
+    // paired tiles (even height) run two nodes per thread along y: bit 0 of
+    // a.pair for the p-half, bit 1 for the u-half
+    const bool pair_p = D >= 2 && (a.pair & 1) && a.ty % 2 == 0;
+    const bool pair_u = D >= 2 && (a.pair & 2) && a.ty % 2 == 0;
     const dim3 pblock((unsigned)a.tx, (unsigned)(a.ty / 2));
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
         bool done = false;
         if constexpr (S::kPairP) {
-            if (pair) {
+            if (pair_p) {
                 k_p_half_pair<D, M, CP><<<grid, pblock, 0, a.stream>>>(a.U, a.P, a.shots, a.n_shots, cp, a.status);
                 done = true;
             }
@@ -56,7 +58,7 @@ static cudaError_t run_grid(const LaunchFp64 &a, const CP &cp)
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
         done = false;
         if constexpr (S::kPairU) {
-            if (pair) {
+            if (pair_u) {
                 k_u_half_pair<D, M, CP><<<grid, pblock, 0, a.stream>>>(a.P, a.U, a.shots, a.n_shots, cp, a.status);
                 done = true;
             }

@@ -60,7 +60,7 @@ struct LaunchFp64 {
     int n_shots;
     int total_tiles;
     int tx, ty;               // tile shape (nodes per tile along x, y)
-    int pair = 0;             // 1: FP64 kernels take two nodes per thread along y
+    int pair = 0;             // FP64 kernels with two nodes per thread along y: bit 0 p-half, bit 1 u-half
     double *P;                // p blocks [q][node] of every shot
     double *U;                // u blocks [comp][q][node] of every shot
     int64_t nsteps;

@@ -19,6 +19,8 @@
 //                  error of every step is carried instead of dropped.
 #pragma once
 
+#include <type_traits>
+
 #include "hl_fp64.cuh"
 #include "hl_split.cuh"
 
@@ -132,14 +134,15 @@ __device__ __forceinline__ bool store_value(double *__restrict__ X, float *__res
     const FF s = split_f64(v);
     Xh[idx] = s.hi;
     if constexpr (COMP) Xl[idx] = s.lo;
-    return !isfinite(v);
+    return nonfinite(v);
 }
 
 // ---------------------------------------------------------------------------
 // One half-step of a mixed mode.  The partner field's shadows for the block's
 // tile plus its one-node halo are staged through shared memory LC slots at a
-// time, in a two-buffer cp.async pipeline: while the block contracts one
-// stage (component c, slots l0 .. l0+LC-1) the next stage is in flight.
+// time, in a two-buffer cp.async pipeline with one barrier per stage: while
+// the block contracts one stage (component c, slots l0 .. l0+LC-1) the next
+// stage is in flight.
 //   PHALF: partner = U (D components), target = P, cell vertices j-1, j;
 //   else : partner = P, target = U components I0 .. I0+NI-1, vertices j, j+1.
 // The staged region is (TX+1)(TY+1)(2) nodes over the axes in use; the
@@ -151,6 +154,7 @@ struct MixedStage {
     static constexpr int LC = M + 1;     // slots per stage (divides NQ)
     static constexpr int NCH = NQ / LC;  // stages per component
 };
+constexpr int kMixedBufs = 2;  // pipeline depth: shared-memory buffers of LC slots
 template <int D>
 __host__ __device__ __forceinline__ int region_nodes(int tx, int ty)
 {
@@ -158,6 +162,20 @@ __host__ __device__ __forceinline__ int region_nodes(int tx, int ty)
     if (D >= 2) r *= ty + 1;
     if (D >= 3) r *= 2;
     return r;
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1.  The
+// stage, slot and output indices of the contraction must be constants so that
+// the structural zeros, the butterfly patterns and the coefficient offsets
+// resolve at compile time; a plain unrolled loop of this size is not
+// guaranteed to be unrolled.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
 }
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src)
@@ -201,7 +219,7 @@ __global__ void __launch_bounds__(256)
     const int nthr = blockDim.x * blockDim.y;
     // offsets inside one slot of every region node, once per block; stored
     // after the two pipeline buffers
-    int *soff = reinterpret_cast<int *>(sm + (size_t)2 * NPART * G::LC * R);
+    int *soff = reinterpret_cast<int *>(sm + (size_t)kMixedBufs * NPART * G::LC * R);
     for (int r = tid; r < R; r += nthr) {
         int gx = x0 + lo + r % RX, gy = y0 + lo + (r / RX) % RY, gz = z0 + lo + r / (RX * RY);
         gx += gx < 0 ? sd.n[0] : (gx >= sd.n[0] ? -sd.n[0] : 0);
@@ -220,7 +238,7 @@ __global__ void __launch_bounds__(256)
         vr[v] = rx + RX * (ry + RY * rz);
     }
     // stage st (component st / NCH, slots (st % NCH) * LC ...) holds the
-    // partner's slots st * LC .. st * LC + LC - 1; it goes to buffer st & 1.
+    // partner's slots st * LC .. st * LC + LC - 1; it goes to buffer st % kMixedBufs.
     // The source pointers advance one stage at a time and are hidden from the
     // optimiser, so no per-stage address is precomputed and kept live.
     const int64_t base = PHALF ? sd.u_off : sd.p_off;
@@ -228,7 +246,7 @@ __global__ void __launch_bounds__(256)
     const float *nh = Sh + base;
     const float *nl = COMP ? Sl + base : nullptr;
     auto prefetch = [&](int st) {
-        float *bh = sm + (size_t)((st & 1) * NPART) * G::LC * R;
+        float *bh = sm + (size_t)((st % kMixedBufs) * NPART) * G::LC * R;
         // a rolled loop over the region: few live addresses at a time
 #pragma unroll 1
         for (int r = tid; r < R; r += nthr) {
@@ -252,54 +270,51 @@ __global__ void __launch_bounds__(256)
     Acc<COMP> acc[NACC];
 #pragma unroll
     for (int e = 0; e < NACC; ++e) acc[e].zero();
-    prefetch(0);
+    // one commit group per stage (empty past the last), kMixedBufs - 1 in flight
 #pragma unroll
-    for (int st = 0; st < NST; ++st) {
-        if (st + 1 < NST) {
-            prefetch(st + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();  // stage st is visible to the whole block
-        if (active) {
-            const int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
-            const float *bh = sm + (size_t)((st & 1) * NPART) * G::LC * R;
-#pragma unroll
-            for (int j = 0; j < G::LC; ++j) {
-                const int l = l0 + j;
-                {
-                    // one slot at a time: keeps the shared-memory reads of
-                    // later slots from being hoisted (register pressure)
-                    asm volatile("" ::: "memory");
-                    Slot<D, COMP> xs;
-#pragma unroll
-                    for (int v = 0; v < S::NV; ++v) {
-                        if constexpr (COMP)
-                            xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
-                        else
-                            xs.x[v] = bh[j * R + vr[v]];
-                    }
-                    if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
-                    if constexpr (PHALF) {
-#pragma unroll
-                        for (int s = 0; s < S::NQ; ++s)
-                            if (coef_nonzero(D, S::n, c, s, l))
-                                xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
-                    } else {
-#pragma unroll
-                        for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-                            for (int s = 0; s < S::NQ; ++s)
-                                if (coef_nonzero(D, S::n, I0 + ii, s, l))
-                                    xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
-                                            bfly_pattern(D, S::n, I0 + ii, s, l));
-                    }
-                }
-            }
-        }
-        __syncthreads();  // buffer st & 1 is free for stage st + 2
+    for (int s0 = 0; s0 < kMixedBufs - 1; ++s0) {
+        if (s0 < NST) prefetch(s0); else cp_async_commit();
     }
+    static_for<0, NST>([&](auto stc) {
+        constexpr int st = decltype(stc)::value;
+        // stage st has landed once at most kMixedBufs - 2 newer groups are
+        // pending; after the barrier it is visible to the whole block, and
+        // every thread has finished stage st-1, whose buffer the prefetch of
+        // stage st + kMixedBufs - 1 then reuses
+        cp_async_wait<kMixedBufs - 2>();
+        __syncthreads();
+        if constexpr (st + kMixedBufs - 1 < NST) prefetch(st + kMixedBufs - 1); else cp_async_commit();
+        if (active) {
+            constexpr int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
+            const float *bh = sm + (size_t)((st % kMixedBufs) * NPART) * G::LC * R;
+            static_for<0, G::LC>([&](auto jc) {
+                constexpr int j = decltype(jc)::value, l = l0 + j;
+                Slot<D, COMP> xs;
+#pragma unroll
+                for (int v = 0; v < S::NV; ++v) {
+                    if constexpr (COMP)
+                        xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
+                    else
+                        xs.x[v] = bh[j * R + vr[v]];
+                }
+                if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
+                if constexpr (PHALF) {
+                    static_for<0, S::NQ>([&](auto sc) {
+                        constexpr int s = decltype(sc)::value;
+                        if constexpr (coef_nonzero(D, S::n, c, s, l))
+                            xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
+                    });
+                } else {
+                    static_for<0, NI * S::NQ>([&](auto ec) {
+                        constexpr int ii = decltype(ec)::value / S::NQ, s = decltype(ec)::value % S::NQ;
+                        if constexpr (coef_nonzero(D, S::n, I0 + ii, s, l))
+                            xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
+                                    bfly_pattern(D, S::n, I0 + ii, s, l));
+                    });
+                }
+            });
+        }
+    });
     if (!active) return;
     bool bad = false;
 #pragma unroll

@@ -63,9 +63,9 @@ static cudaError_t run_mixed_t(const LaunchFp64 &a)
     constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 64;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
     const int region = region_nodes<D>(a.tx, a.ty);
-    // two pipeline buffers of LC slots each (hi, and lo for the compensated
-    // mode), then one offset per region node
-    const size_t smem = ((size_t)2 * MixedStage<D, M>::LC * (COMP ? 2 : 1) + 1) * region * sizeof(float);
+    // kMixedBufs pipeline buffers of LC slots each (hi, and lo for the
+    // compensated mode), then one offset per region node
+    const size_t smem = ((size_t)kMixedBufs * MixedStage<D, M>::LC * (COMP ? 2 : 1) + 1) * region * sizeof(float);
     cudaError_t e;
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);

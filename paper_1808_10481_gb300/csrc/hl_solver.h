@@ -13,10 +13,12 @@
 namespace hl {
 
 // tile (thread block) shapes the autotuner chooses from: (TX, TY)
-// {nodes per tile along x, along y, paired}: paired tiles run the FP64
-// kernels with two nodes per thread along y (blocks of x * y/2 threads)
-constexpr int kTiles[][3] = {{128, 1, 0}, {256, 1, 0}, {64, 2, 0}, {32, 4, 0}, {32, 8, 0}, {64, 4, 0},
-                             {16, 8, 0},  {16, 16, 0}, {32, 4, 1}, {32, 8, 1}, {64, 4, 1}, {16, 16, 1}};
+// {nodes per tile along x, along y, pairing}: pairing bit 0 runs the FP64
+// p-half, bit 1 the u-half, with two nodes per thread along y (blocks of
+// x * y/2 threads)
+constexpr int kTiles[][3] = {{128, 1, 0}, {256, 1, 0}, {64, 2, 0}, {32, 4, 0}, {32, 8, 0},
+                             {64, 4, 0},  {16, 8, 0},  {16, 16, 0}, {32, 4, 3}, {32, 8, 3},
+                             {64, 4, 3},  {16, 16, 3}, {32, 8, 1},  {64, 4, 1}};
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
 static_assert(kNumTiles == HL_NUM_TILES, "tile table and header disagree");
 
