@@ -254,7 +254,10 @@ def run_aux(args, rank=0, world=1, dist=None):
         dof = (d + 1) * (m + 1) ** d * nnode
         modes = {}
         ref_p = None
-        for name, mode in (("fp64", hl.HL_FP64), ("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)):
+        mode_list = [("fp64", hl.HL_FP64), ("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)]
+        if d == 2:
+            mode_list.append(("tc_split", hl.HL_TC_SPLIT))
+        for name, mode in mode_list:
             h = hl.hl_create(d, m, ncell, dt)
             hl.hl_set_stream(h, stream)
             hl.hl_set_precision(h, mode)
@@ -291,7 +294,7 @@ def run_aux(args, rank=0, world=1, dist=None):
         except OSError:
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        for name in ("fp32", "fp32_comp"):
+        for name in [k for k in modes if k != "fp64"]:
             modes[name]["roofline"] = {"bound": "hbm", "achieved": modes[name]["hbm_gbs"], "peak": hbm,
                                        "unit": "GB/s", "frac": modes[name]["hbm_gbs"] / hbm,
                                        "peak_source": "measured" if peaks else "fallback"}
@@ -322,7 +325,7 @@ def run_aux(args, rank=0, world=1, dist=None):
                                "l2_err_p_vs_exact": I.l2_error(d, c2, pg2, ex2.p)})
             ladder.append({"n": ncell[0], "steps": lf, "ms_run": modes["fp64"]["ms_per_step"] * lf,
                            "l2_err_p_vs_exact": modes["fp64"]["l2_err_p_vs_exact"]})
-            for name in ("fp32", "fp32_comp"):
+            for name in [k for k in modes if k != "fp64"]:
                 e = modes[name]["l2_err_p_vs_exact"]
                 ok = [r for r in ladder if r["l2_err_p_vs_exact"] <= e * 1.001]  # equal within 0.1%
                 if ok:
@@ -332,7 +335,7 @@ def run_aux(args, rank=0, world=1, dist=None):
                         "n": r["n"], "ms_run": r["ms_run"], "l2_err_p_vs_exact": r["l2_err_p_vs_exact"],
                         "ms_run_mode": t_mode, "speedup_vs_fp64_at_equal_error": r["ms_run"] / t_mode}
             out["fp64_error_ladder"] = ladder
-        out.update({"workload": args.workload, "value": modes["fp32_comp"]["value"],
+        out.update({"workload": args.workload, "value": modes["tc_split" if "tc_split" in modes else "fp32_comp"]["value"],
                     "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
                     "modes": modes})
     elif args.workload == "learned":

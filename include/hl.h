@@ -78,10 +78,17 @@ enum {
     HL_FP32 = 1,         /* interpolation + evolution contraction on the FP32
                             pipe: data and operator rounded to binary32, FP32
                             accumulation                                     */
-    HL_FP32_COMP = 2     /* as HL_FP32 plus a split-precision correction: data
-                            and operator split into binary32 hi + lo parts,
-                            hi*hi accumulated apart from hi*lo + lo*hi, the two
-                            sums added in binary64                           */
+    HL_FP32_COMP = 2,    /* as HL_FP32 with a split-precision correction:
+                            data and operator as binary32 hi + lo pairs and
+                            float-float arithmetic throughout (error-free
+                            TwoSum / TwoProduct), about 48 significant bits  */
+    HL_TC_SPLIT = 3      /* dim = 2 only: the contraction as exact BF16
+                            tensor-core products (mma.sync, FP32 accumulate):
+                            data (their hi + lo pairs) and operator scaled by
+                            powers of two and cut into 6 base-256 digits; the
+                            digit pairs of the 7 leading levels are summed,
+                            each level exactly, then in float-float; about
+                            46 bits below the block maximum               */
 };
 
 /*
@@ -213,9 +220,9 @@ int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile, double *m
 
 /*
  * hl_set_precision -- select the arithmetic mode (HL_FP64, HL_FP32,
- * HL_FP32_COMP).  The FP32 modes need m <= 3 (m <= 2 in 3D) and, on a batch, the same
- * dt/h on every shot; they return HL_EINVAL otherwise.  Takes effect at the
- * next hl_step.
+ * HL_FP32_COMP, HL_TC_SPLIT).  The mixed modes need m <= 3 (m <= 2 in 3D,
+ * HL_TC_SPLIT dim = 2 only) and, on a batch, the same dt/h on every shot;
+ * they return HL_EINVAL otherwise.  Takes effect at the next hl_step.
  */
 int hl_set_precision(hl_solver *h, int mode);
 

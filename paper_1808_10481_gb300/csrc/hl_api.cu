@@ -78,6 +78,8 @@ static void release(hl_solver *h)
     if (h->Pl) cudaFree(h->Pl);
     if (h->Uh) cudaFree(h->Uh);
     if (h->Ul) cudaFree(h->Ul);
+    if (h->tc_digits) cudaFree(h->tc_digits);
+    if (h->tc_expo) cudaFree(h->tc_expo);
     delete h;
 }
 
@@ -244,8 +246,10 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
 {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (mode != HL_FP64 && mode != HL_FP32 && mode != HL_FP32_COMP)
+    if (mode != HL_FP64 && mode != HL_FP32 && mode != HL_FP32_COMP && mode != HL_TC_SPLIT)
         return set_err(h, HL_EINVAL, "unknown precision mode");
+    if (mode == HL_TC_SPLIT && h->dim != 2)
+        return set_err(h, HL_EINVAL, "the tensor-core split mode supports dim = 2");
     if (mode != HL_FP64) {
         if (h->m > 3 || (h->dim == 3 && h->m > 2))
             return set_err(h, HL_EINVAL, "mixed precision supports m <= 3 (m <= 2 in 3D)");
@@ -262,10 +266,20 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         const size_t n = (size_t)h->p_elems;
         if (!h->Ph) HL_CK(h, cudaMalloc(&h->Ph, n * sizeof(float)));
         if (!h->Uh) HL_CK(h, cudaMalloc(&h->Uh, n * h->dim * sizeof(float)));
-        if (mode == HL_FP32_COMP) {
+        if (mode == HL_FP32_COMP || mode == HL_TC_SPLIT) {
             if (!h->Pl) HL_CK(h, cudaMalloc(&h->Pl, n * sizeof(float)));
             if (!h->Ul) HL_CK(h, cudaMalloc(&h->Ul, n * h->dim * sizeof(float)));
         }
+    }
+    if (mode == HL_TC_SPLIT && !h->tc_digits) {
+        std::vector<uint16_t> dig;
+        std::vector<int> ex;
+        if (!build_tc_tables(h->m, h->coef.data(), dig, ex))
+            return set_err(h, HL_EINVAL, "tensor-core tables need m <= 3");
+        HL_CK(h, cudaMalloc(&h->tc_digits, dig.size() * sizeof(uint16_t)));
+        HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
+        HL_CK(h, cudaMemcpy(h->tc_digits, dig.data(), dig.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        HL_CK(h, cudaMemcpy(h->tc_expo, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
     }
     h->precision = mode;
     return HL_OK;
@@ -439,11 +453,14 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.Uh = h->Uh;
     a.Ul = h->Ul;
     a.p_elems = h->p_elems;
+    a.tc_digits = h->tc_digits;
+    a.tc_expo = h->tc_expo;
     return a;
 }
 
 static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 {
+    if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : cudaErrorInvalidValue;
     if (a.precision != HL_FP64) {
         switch (dim) {
         case 1: return launch_mixed_d1(a);

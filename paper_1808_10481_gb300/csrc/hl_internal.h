@@ -74,11 +74,27 @@ struct LaunchFp64 {
     bool *used_small;         // set to whether the single-CTA path ran
     const SourceDesc *src;    // point sources injected after every p-half (may be NULL)
     int64_t step0;            // index of the first step (source time)
-    int precision;            // HL_FP64 (0), HL_FP32 (1), HL_FP32_COMP (2)
-    // binary32 shadows of P and U for the mixed modes (lo only for HL_FP32_COMP)
+    int precision;            // HL_FP64 (0), HL_FP32 (1), HL_FP32_COMP (2), HL_TC_SPLIT (3)
+    // binary32 shadows of P and U for the mixed modes (lo for HL_FP32_COMP and HL_TC_SPLIT)
     float *Ph, *Pl, *Uh, *Ul;
     int64_t p_elems;          // elements of P over all shots (U has dim times more)
+    // HL_TC_SPLIT digit tables (see build_tc_tables): device, kTcOps operators
+    const uint16_t *tc_digits = nullptr;
+    const int *tc_expo = nullptr;
 };
+
+// Tensor-core split mode (HL_TC_SPLIT, dim = 2, m <= 3).  Each operator is the
+// vertex form of the fused half-step operator, B[k][n] with k = (partner
+// component, vertex, slot) padded to 16 slots and n = output slot (16); every
+// column n is scaled by 2^-e_n and cut into kTcDigits balanced base-256
+// digits (signed integers in [-128, 127], exact in BF16).  Operators: 0 the
+// p-half (K = 128), 1 + i the u-half's component i (K = 64).
+constexpr int kTcDigits = 6;                  // digits per operand (46 bits)
+constexpr int kTcOps = 3;
+constexpr int kTcN = 16;                      // output columns per operator
+constexpr int kTcKS = 136;                    // row stride (bf16) of a digit row: 128 + 8 padding
+constexpr int kTcOpElems = kTcDigits * kTcN * kTcKS;
+bool build_tc_tables(int m, const double *coef, std::vector<uint16_t> &digits, std::vector<int> &expo);
 
 cudaError_t launch_fp64_d1(const LaunchFp64 &a);
 cudaError_t launch_fp64_d2(const LaunchFp64 &a);
@@ -86,6 +102,7 @@ cudaError_t launch_fp64_d3(const LaunchFp64 &a);
 cudaError_t launch_mixed_d1(const LaunchFp64 &a);  // precision 1 or 2, m <= 3
 cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
+cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
 
 // message returned by hl_last_error(NULL) for calls that have no handle
 void set_handleless_error(const char *msg);

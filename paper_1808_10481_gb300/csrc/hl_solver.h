@@ -77,6 +77,8 @@ struct hl_solver {
     // point sources
     hl::SourceDesc src;
     float *Ph = nullptr, *Pl = nullptr, *Uh = nullptr, *Ul = nullptr;  // mixed-precision shadows
+    uint16_t *tc_digits = nullptr;  // HL_TC_SPLIT operator digit tables (kTcOps operators)
+    int *tc_expo = nullptr;         // and their column exponents
     int *src_node = nullptr, *src_shot = nullptr;
     double *src_table = nullptr;
 };

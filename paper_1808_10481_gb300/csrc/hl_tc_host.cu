@@ -1,0 +1,82 @@
+// Host side of the tensor-core split mode: the digit tables of the operator.
+//
+// The kernels contract the partner data at the 2^d = 4 cell vertices
+// directly (no butterfly).  The vertex form of the fused operator follows
+// from the butterfly form: the butterfly entry x[pat] weights vertex v by
+// prod over axes k with v_k = 1 of (bit k of pat ? -1 : +1), so
+//   W[c][v][l][s] = coef(c, l, s) * prod_{k: v_k = 1, pat_k = 1} (-1),
+// pat = bfly_pattern(c, s, l), and zero where the structural-zero rule holds.
+//
+// Exact split (an Ozaki-type scheme): column n is scaled by 2^-e_n with
+// max_k |W[k][n]| < 2^e_n, rounded to an integer of 46 bits, and written as
+// kTcDigits balanced base-256 digits; digit j carries weight 2^(8 (5 - j)).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "hl_fp64.cuh"
+#include "hl_internal.h"
+
+namespace hl {
+
+static uint16_t bf16_of_small_int(int d)
+{
+    const float f = (float)d;  // |d| <= 128: 8 significant bits, exact in bfloat16
+    uint32_t b;
+    std::memcpy(&b, &f, sizeof b);
+    return (uint16_t)(b >> 16);
+}
+
+// balanced base-256 digits of |X| < 2^46, most significant first
+static void digits_of(int64_t X, int *d)
+{
+    for (int j = kTcDigits - 1; j >= 0; --j) {
+        int64_t r = X & 255;
+        if (r >= 128) r -= 256;
+        d[j] = (int)r;
+        X = (X - r) / 256;  // exact
+    }
+}
+
+bool build_tc_tables(int m, const double *coef, std::vector<uint16_t> &digits, std::vector<int> &expo)
+{
+    if (m < 0 || m > 3) return false;
+    const int D = 2, n = m + 1, NQ = n * n;
+    digits.assign((size_t)kTcOps * kTcOpElems, 0);
+    expo.assign((size_t)kTcOps * kTcN, 0);
+    for (int op = 0; op < kTcOps; ++op) {
+        // dense vertex-form operator W[k][s], k padded (16 slots per (component, vertex))
+        std::vector<double> W((size_t)128 * kTcN, 0.0);
+        const int ncomp = op == 0 ? D : 1;  // partner components: u (D) for the p-half, p for the u-half
+        for (int c = 0; c < ncomp; ++c) {
+            const int i = op == 0 ? c : op - 1;  // direction of the operator block
+            for (int v = 0; v < 4; ++v)
+                for (int l = 0; l < NQ; ++l)
+                    for (int s = 0; s < NQ; ++s) {
+                        if (!coef_nonzero(D, n, i, s, l)) continue;
+                        const int pat = bfly_pattern(D, n, i, s, l);
+                        const double sign = (__builtin_popcount(v & pat) & 1) ? -1.0 : 1.0;
+                        W[(size_t)((c * 4 + v) * 16 + l) * kTcN + s] = sign * coef[coef_index(NQ, i, l, s)];
+                    }
+        }
+        for (int s = 0; s < kTcN; ++s) {
+            double mx = 0.0;
+            for (int k = 0; k < 128; ++k) mx = std::fmax(mx, std::fabs(W[(size_t)k * kTcN + s]));
+            int e = 0;
+            if (mx > 0.0) std::frexp(mx, &e);  // mx < 2^e
+            expo[(size_t)op * kTcN + s] = e;
+            for (int k = 0; k < 128; ++k) {
+                const double w = W[(size_t)k * kTcN + s];
+                const int64_t X = (int64_t)std::llround(std::ldexp(w, 46 - e));
+                int d[kTcDigits];
+                digits_of(X, d);
+                for (int j = 0; j < kTcDigits; ++j)
+                    digits[(size_t)op * kTcOpElems + ((size_t)j * kTcN + s) * kTcKS + k] = bf16_of_small_int(d[j]);
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace hl

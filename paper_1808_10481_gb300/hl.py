@@ -20,6 +20,7 @@ HL_OK, HL_EINVAL, HL_ENOMEM, HL_ECUDA, HL_ETIMEOUT, HL_ENONFINITE, HL_ESTATE = 0
 HL_FP64 = 0
 HL_FP32 = 1
 HL_FP32_COMP = 2
+HL_TC_SPLIT = 3
 HL_OPT_KERNEL_PATH = 1
 HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3

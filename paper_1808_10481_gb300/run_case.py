@@ -29,7 +29,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 single CTA, 2 grid launches")
     ap.add_argument("--init", choices=["gaussian", "random", "zero"], default="random")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_comp"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_comp", "tc_split"], default="fp64")
     ap.add_argument("--tile", type=int, default=-1, help="tile shape index (HL_OPT_TILE); -1 keeps the default")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="instead of stepping: this many rows of MLP training steps (loss, gradient, Adam)")
@@ -64,7 +64,8 @@ def main(argv=None):
             hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, args.path)
         if args.tile >= 0:
             hl.hl_set_option(h, hl.HL_OPT_TILE, args.tile)
-        hl.hl_set_precision(h, {"fp64": hl.HL_FP64, "fp32": hl.HL_FP32, "fp32_comp": hl.HL_FP32_COMP}[args.precision])
+        hl.hl_set_precision(h, {"fp64": hl.HL_FP64, "fp32": hl.HL_FP32, "fp32_comp": hl.HL_FP32_COMP,
+                                 "tc_split": hl.HL_TC_SPLIT}[args.precision])
         hl.hl_set_initial(h, p, u)
         if args.warmup:
             hl.hl_step(h, args.warmup)
