@@ -81,32 +81,33 @@ __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, uint32_t b
 __device__ __forceinline__ int tc_word(int row, int w) { return row * 8 + (w ^ (((row >> 2) & 1) << 2)); }
 
 // Shared memory of one block (bytes) for a tile of tx x ty nodes.
-__host__ __device__ constexpr size_t tc_smem_bytes(int tx, int ty, int nq)
+__host__ __device__ constexpr size_t tc_smem_bytes(int tx, int ty, int nq, int nops)
 {
-    return (size_t)kTcOpElems * 2                            // operator digits
+    return (size_t)nops * kTcOpElems * 2                     // operator digits
            + (size_t)kTcDigits * (tx + 1) * (ty + 1) * 32     // partner digits
            + (size_t)2 * nq * (tx + 1) * (ty + 1) * 4          // staged partner values (hi, lo)
            + (size_t)(tx + 1) * (ty + 1) * 4 + 8 * 4;          // region offsets, reduction
 }
 
-// One half-step.  PHALF: partner u (2 components), output p; else partner p,
-// output u component `oc`.  Bd / Be: the operator's digits and column
-// exponents.  MTW: 16-node row blocks per warp (tiles of 128 or 256 nodes).
+// One half-step.  PHALF: partner u (2 components), output p (operator 0); else
+// partner p, outputs u components 0 and 1 (operators 1, 2), staged once.  Bd /
+// Be: the operators' digits and column exponents, back to back.  MTW: 16-node
+// row blocks per warp (tiles of 128 or 256 nodes).
 template <int M, bool PHALF, int MTW>
 // two blocks per SM for 128-node tiles (measured 1.5x faster than one block
 // with more registers); 256-node tiles hold twice the accumulators and run one
 __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
     k_half_tc(const float *__restrict__ Sh, const float *__restrict__ Sl, double *__restrict__ X,
               float *__restrict__ Xh, float *__restrict__ Xl, const ShotDesc *__restrict__ shots, int n_shots,
-              int tx, int ty, const uint16_t *__restrict__ Bd, const int *__restrict__ Be, int oc,
-              unsigned *status)
+              int tx, int ty, const uint16_t *__restrict__ Bd, const int *__restrict__ Be, unsigned *status)
 {
     constexpr int NQ = (M + 1) * (M + 1);
-    constexpr int NCIN = PHALF ? 2 : 1;
+    constexpr int NCIN = PHALF ? 2 : 1;  // partner components
+    constexpr int NOUT = PHALF ? 1 : 2;  // output components (operators)
     extern __shared__ __align__(16) unsigned char tc_sm[];
     const int RX = tx + 1, R = (tx + 1) * (ty + 1);
     uint16_t *Bs = reinterpret_cast<uint16_t *>(tc_sm);
-    uint32_t *As = reinterpret_cast<uint32_t *>(Bs + kTcOpElems);  // [digit][region node] rows of 8 words
+    uint32_t *As = reinterpret_cast<uint32_t *>(Bs + NOUT * kTcOpElems);  // [digit][region node] rows of 8 words
     float *Fh = reinterpret_cast<float *>(As + (size_t)kTcDigits * R * 8);  // [slot][region node]
     float *Fl = Fh + (size_t)NQ * R;
     int *soff = reinterpret_cast<int *>(Fl + (size_t)NQ * R);
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
     const int lo = PHALF ? -1 : 0;
 
     // operator digits (16-byte copies), region offsets (periodic), zero padded slots
-    for (int e = tid; e < kTcOpElems / 8; e += kTcThreads)
+    for (int e = tid; e < NOUT * kTcOpElems / 8; e += kTcThreads)
         reinterpret_cast<uint4 *>(Bs)[e] = __ldg(reinterpret_cast<const uint4 *>(Bd) + e);
     for (int r = tid; r < R; r += kTcThreads) {
         int gx = x0 + lo + r % RX, gy = y0 + lo + r / RX;
@@ -135,11 +136,13 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
     if constexpr (NQ < 16) {
         for (int e = tid; e < kTcDigits * R * 8; e += kTcThreads) As[e] = 0u;
     }
-    int en[2][2];  // exponents of this thread's output columns
+    int en[NOUT][2][2];  // exponents of this thread's output columns
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
+    for (int o = 0; o < NOUT; ++o)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) en[nt][q] = __ldg(Be + nt * 8 + 2 * t + q);
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) en[o][nt][q] = __ldg(Be + o * kTcN + nt * 8 + 2 * t + q);
 
     const int nmt = tx * ty / 16;
     FF tot[MTW][2][4];
@@ -149,6 +152,34 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) tot[a][nt][e] = FF{0.f, 0.f};
+
+    // epilogue: add the increments of output component oc to the binary64 node
+    // data, refresh the shadows, and clear the sums
+    bool bad = false;
+    auto store_out = [&](int oc) {
+#pragma unroll
+        for (int a = 0; a < MTW; ++a) {
+            const int mt = warp + 8 * a;
+            if (mt >= nmt) continue;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = mt * 16 + g + (e >= 2 ? 8 : 0);
+                    const int s = nt * 8 + 2 * t + (e & 1);
+                    const int gx = x0 + q % tx, gy = y0 + q / tx;
+                    if (s < NQ && gx < sd.n[0] && gy < sd.n[1]) {
+                        const int64_t node = gx + (int64_t)sd.n[0] * gy;
+                        const int64_t idx = (PHALF ? sd.p_off + (int64_t)s * sd.nnode
+                                                   : sd.u_off + (int64_t)(oc * NQ + s) * sd.nnode) + node;
+                        Acc<true> inc;
+                        inc.v = tot[a][nt][e];
+                        bad |= store_value<true>(X, Xh, Xl, idx, inc.to_f64());
+                    }
+                    tot[a][nt][e] = FF{0.f, 0.f};
+                }
+        }
+    };
 
     const int64_t base0 = PHALF ? sd.u_off : sd.p_off;
     static_for<0, NCIN>([&](auto cc) {
@@ -200,6 +231,9 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
         }
         __syncthreads();
         // exact digit products on the tensor cores, one 16-node row block at a time
+        static_for<0, NOUT>([&](auto occ) {
+        constexpr int o = decltype(occ)::value;
+        const uint16_t *Bo = Bs + o * kTcOpElems;
         static_for<0, MTW>([&](auto ac) {
             constexpr int a = decltype(ac)::value;
             const int mt = warp + 8 * a;
@@ -217,7 +251,7 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                     static_for<0, 4>([&](auto vc) {
                         constexpr int v = decltype(vc)::value;
                         const int dv = (v & 1) + RX * (v >> 1);
-                        const uint16_t *bcol = Bs + (size_t)(nt * 8 + g) * kTcKS + (c * 4 + v) * 16 + 2 * t;
+                        const uint16_t *bcol = Bo + (size_t)(nt * 8 + g) * kTcKS + (c * 4 + v) * 16 + 2 * t;
                         static_for<0, kTcDigits>([&](auto ic) {
                             constexpr int i = decltype(ic)::value;
                             const int ra = i * R + rq0 + dv, rb = i * R + rq1 + dv;
@@ -235,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                     // levels -> float-float, scaled by 2^(E + e_n - 12 - 8 L) (exact)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int k0 = E + en[nt][e & 1] - 12;
+                        const int k0 = E + en[o][nt][e & 1] - 12;
 #pragma unroll
                         for (int L = 0; L < kTcLevels; ++L) {
                             const float val = acc[L][e] * pow2f(k0 - 8 * L);
@@ -247,31 +281,11 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                 });
             }
         });
+        if constexpr (!PHALF) store_out(o);  // the single partner component is complete
+        });
     });
 
-    // epilogue: add the increments to the binary64 node data and refresh the shadows
-    bool bad = false;
-#pragma unroll
-    for (int a = 0; a < MTW; ++a) {
-        const int mt = warp + 8 * a;
-        if (mt >= nmt) continue;
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int q = mt * 16 + g + (e >= 2 ? 8 : 0);
-                const int s = nt * 8 + 2 * t + (e & 1);
-                const int gx = x0 + q % tx, gy = y0 + q / tx;
-                if (s < NQ && gx < sd.n[0] && gy < sd.n[1]) {
-                    const int64_t node = gx + (int64_t)sd.n[0] * gy;
-                    const int64_t idx = (PHALF ? sd.p_off + (int64_t)s * sd.nnode
-                                               : sd.u_off + (int64_t)(oc * NQ + s) * sd.nnode) + node;
-                    Acc<true> inc;
-                    inc.v = tot[a][nt][e];
-                    bad |= store_value<true>(X, Xh, Xl, idx, inc.to_f64());
-                }
-            }
-    }
+    if constexpr (PHALF) store_out(0);
     report_nonfinite(bad, status);
 }
 
@@ -279,7 +293,7 @@ template <int M, int MTW>
 static cudaError_t run_tc_t(const LaunchFp64 &a)
 {
     constexpr int NQ = (M + 1) * (M + 1);
-    const size_t smem = tc_smem_bytes(a.tx, a.ty, NQ);
+    const size_t smem = tc_smem_bytes(a.tx, a.ty, NQ, 2);  // the u-half holds two operators
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     static std::atomic<uint64_t> opted_in{0};
     int dev = 0;
@@ -300,17 +314,16 @@ static cudaError_t run_tc_t(const LaunchFp64 &a)
     const dim3 grid((unsigned)a.total_tiles);
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        k_half_tc<M, true, MTW><<<grid, kTcThreads, smem, a.stream>>>(a.Uh, a.Ul, a.P, a.Ph, a.Pl, a.shots, a.n_shots,
-                                                                      a.tx, a.ty, a.tc_digits, a.tc_expo, 0, a.status);
+        k_half_tc<M, true, MTW><<<grid, kTcThreads, tc_smem_bytes(a.tx, a.ty, NQ, 1), a.stream>>>(
+            a.Uh, a.Ul, a.P, a.Ph, a.Pl, a.shots, a.n_shots, a.tx, a.ty, a.tc_digits, a.tc_expo, a.status);
         if (a.src && a.src->active) {
             if ((e = launch_source(*a.src, a.shots, a.P, NQ, a.step0 + st, a.stream, a.Ph, a.Pl)) != cudaSuccess)
                 return e;
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
-        for (int oc = 0; oc < 2; ++oc)
-            k_half_tc<M, false, MTW><<<grid, kTcThreads, smem, a.stream>>>(
-                a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots, a.n_shots, a.tx, a.ty, a.tc_digits + (size_t)(1 + oc) * kTcOpElems,
-                a.tc_expo + (1 + oc) * kTcN, oc, a.status);
+        k_half_tc<M, false, MTW><<<grid, kTcThreads, smem, a.stream>>>(a.Ph, a.Pl, a.U, a.Uh, a.Ul, a.shots, a.n_shots,
+                                                                       a.tx, a.ty, a.tc_digits + kTcOpElems,
+                                                                       a.tc_expo + kTcN, a.status);
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();
