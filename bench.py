@@ -335,7 +335,9 @@ def run_aux(args, rank=0, world=1, dist=None):
                         "n": r["n"], "ms_run": r["ms_run"], "l2_err_p_vs_exact": r["l2_err_p_vs_exact"],
                         "ms_run_mode": t_mode, "speedup_vs_fp64_at_equal_error": r["ms_run"] / t_mode}
             out["fp64_error_ladder"] = ladder
-        out.update({"workload": args.workload, "value": modes["tc_split" if "tc_split" in modes else "fp32_comp"]["value"],
+        # headline of the line: the fastest mode that keeps the FP64 solution (the split modes)
+        best = max([k for k in ("fp32_comp", "tc_split") if k in modes], key=lambda k: modes[k]["value"])
+        out.update({"workload": args.workload, "value": modes[best]["value"], "value_mode": best,
                     "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
                     "modes": modes})
     elif args.workload == "learned":

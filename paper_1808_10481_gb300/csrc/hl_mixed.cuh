@@ -275,46 +275,75 @@ __global__ void __launch_bounds__(256)
     for (int s0 = 0; s0 < kMixedBufs - 1; ++s0) {
         if (s0 < NST) prefetch(s0); else cp_async_commit();
     }
-    static_for<0, NST>([&](auto stc) {
-        constexpr int st = decltype(stc)::value;
-        // stage st has landed once at most kMixedBufs - 2 newer groups are
-        // pending; after the barrier it is visible to the whole block, and
-        // every thread has finished stage st-1, whose buffer the prefetch of
-        // stage st + kMixedBufs - 1 then reuses
-        cp_async_wait<kMixedBufs - 2>();
-        __syncthreads();
-        if constexpr (st + kMixedBufs - 1 < NST) prefetch(st + kMixedBufs - 1); else cp_async_commit();
-        if (active) {
-            constexpr int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
-            const float *bh = sm + (size_t)((st % kMixedBufs) * NPART) * G::LC * R;
-            static_for<0, G::LC>([&](auto jc) {
-                constexpr int j = decltype(jc)::value, l = l0 + j;
-                Slot<D, COMP> xs;
+    // The float-float 3D p-half (27 stages of 27 outputs) fully unrolled is
+    // about 30 k instructions and runs slower (instruction fetch) than this
+    // rolled loop, which resolves the stage's coefficients at run time.
+    constexpr bool kRolled = COMP && D == 3 && PHALF;
+    if constexpr (kRolled) {
+#pragma unroll 1
+        for (int st = 0; st < NST; ++st) {
+            cp_async_wait<kMixedBufs - 2>();
+            __syncthreads();
+            if (st + kMixedBufs - 1 < NST) prefetch(st + kMixedBufs - 1); else cp_async_commit();
+            if (active) {
+                const int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
+                const float *bh = sm + (size_t)((st % kMixedBufs) * NPART) * G::LC * R;
 #pragma unroll
-                for (int v = 0; v < S::NV; ++v) {
-                    if constexpr (COMP)
-                        xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
-                    else
-                        xs.x[v] = bh[j * R + vr[v]];
-                }
-                if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
-                if constexpr (PHALF) {
-                    static_for<0, S::NQ>([&](auto sc) {
-                        constexpr int s = decltype(sc)::value;
-                        if constexpr (coef_nonzero(D, S::n, c, s, l))
+                for (int j = 0; j < G::LC; ++j) {
+                    const int l = l0 + j;
+                    Slot<D, COMP> xs;
+#pragma unroll
+                    for (int v = 0; v < S::NV; ++v) xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
+                    butterfly_ff<D>(xs.x);
+#pragma unroll
+                    for (int s = 0; s < S::NQ; ++s)
+                        if (coef_nonzero(D, S::n, c, s, l))
                             xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
-                    });
-                } else {
-                    static_for<0, NI * S::NQ>([&](auto ec) {
-                        constexpr int ii = decltype(ec)::value / S::NQ, s = decltype(ec)::value % S::NQ;
-                        if constexpr (coef_nonzero(D, S::n, I0 + ii, s, l))
-                            xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
-                                    bfly_pattern(D, S::n, I0 + ii, s, l));
-                    });
                 }
-            });
+            }
         }
-    });
+    } else {
+        static_for<0, NST>([&](auto stc) {
+            constexpr int st = decltype(stc)::value;
+            // stage st has landed once at most kMixedBufs - 2 newer groups are
+            // pending; after the barrier it is visible to the whole block, and
+            // every thread has finished stage st-1, whose buffer the prefetch of
+            // stage st + kMixedBufs - 1 then reuses
+            cp_async_wait<kMixedBufs - 2>();
+            __syncthreads();
+            if constexpr (st + kMixedBufs - 1 < NST) prefetch(st + kMixedBufs - 1); else cp_async_commit();
+            if (active) {
+                constexpr int c = st / G::NCH, l0 = (st % G::NCH) * G::LC;
+                const float *bh = sm + (size_t)((st % kMixedBufs) * NPART) * G::LC * R;
+                static_for<0, G::LC>([&](auto jc) {
+                    constexpr int j = decltype(jc)::value, l = l0 + j;
+                    Slot<D, COMP> xs;
+#pragma unroll
+                    for (int v = 0; v < S::NV; ++v) {
+                        if constexpr (COMP)
+                            xs.x[v] = FF{bh[j * R + vr[v]], bh[(G::LC + j) * R + vr[v]]};
+                        else
+                            xs.x[v] = bh[j * R + vr[v]];
+                    }
+                    if constexpr (COMP) butterfly_ff<D>(xs.x); else butterfly_f<D>(xs.x);
+                    if constexpr (PHALF) {
+                        static_for<0, S::NQ>([&](auto sc) {
+                            constexpr int s = decltype(sc)::value;
+                            if constexpr (coef_nonzero(D, S::n, c, s, l))
+                                xs.madd(acc[s], cf, coef_index(S::NQ, c, l, s), bfly_pattern(D, S::n, c, s, l));
+                        });
+                    } else {
+                        static_for<0, NI * S::NQ>([&](auto ec) {
+                            constexpr int ii = decltype(ec)::value / S::NQ, s = decltype(ec)::value % S::NQ;
+                            if constexpr (coef_nonzero(D, S::n, I0 + ii, s, l))
+                                xs.madd(acc[ii * S::NQ + s], cf, coef_index(S::NQ, I0 + ii, l, s),
+                                        bfly_pattern(D, S::n, I0 + ii, s, l));
+                        });
+                    }
+                });
+            }
+        });
+    }
     if (!active) return;
     bool bad = false;
 #pragma unroll
