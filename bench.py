@@ -387,7 +387,7 @@ def run_aux(args, rank=0, world=1, dist=None):
 
 def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
     """Learned coarse-grid correction at the workload's scale: coarse 256^2 vs fine 1024^2,
-    m = 3, seeded Gaussian pulses and Ricker sources; the fine FP64 solver is the judge."""
+    m = 3, seeded Gaussian pulses and Ricker sources; the fine FP64 solver is the reference."""
     import numpy as np
     import torch
 
@@ -492,7 +492,7 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
     return {
         "workload": "learned",
         "value": dof_c / ((t_coarse / n_seeds + corr_ms / n_test) / 1e3),
-        "config": {"workload": f"learned coarse-grid correction: 2D m=3, coarse 256^2 vs fine 1024^2 (FP64 judge), "
+        "config": {"workload": f"learned coarse-grid correction: 2D m=3, coarse 256^2 vs fine 1024^2 (fine FP64 solver as reference), "
                                f"{n_train} training + {n_test} held-out seeds (Gaussian pulses width U[0.012,0.025] "
                                f"and Ricker sources f0 U[10,20]), horizon {horizon} coarse steps",
                    "mlp": "288-128-128-16, BF16 tensor-core products, FP32 accumulate, Adam",

@@ -11,7 +11,7 @@ operator H from ``hermite.py``.
 Two builds of the same source: ``prec="f64"`` (IEEE binary64, the paper's
 precision and the timed CPU baseline) and ``prec="dd"`` (double-double, about
 106 significant bits, ``dd.hpp``; the same bits on every platform).  Long runs
-are judged against the ``dd`` build, because the binary64 build's own
+are compared with the ``dd`` build, because the binary64 build's own
 accumulated rounding after hundreds of steps (about 1e-12 to 5e-12 relative on
 the 1D and 2D workloads) is as large as the parity bar.  Arrays passed to a
 ``dd`` call become (hi, lo = 0) pairs; results come back rounded to float64.
@@ -39,7 +39,7 @@ _DEPS = [_SRC, os.path.join(_HERE, "dd.hpp")]
 
 
 class DD(ctypes.Structure):
-    """A double-double scalar as the judge build passes it by value."""
+    """A double-double scalar as the double-double build passes it by value."""
     _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double)]
 _libs: dict = {}
 

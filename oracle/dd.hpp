@@ -1,4 +1,4 @@
-// Double-double numbers for the oracle's judge build (C++ only).
+// Double-double numbers for the oracle's double-double build (C++ only).
 //
 // A value is hi + lo with |lo| <= ulp(hi)/2, about 106 significant bits,
 // carried by IEEE binary64 operations and the error-free transformations

@@ -50,7 +50,7 @@
 /* The source is precision-generic.  The default build (C) uses IEEE
  * binary64, the paper's precision (Section 6).  Built as C++ with -DORC_DD it
  * uses double-double arithmetic (dd.hpp, about 106 significant bits): the same
- * steps with a far smaller rounding error, used to judge long runs against a
+ * steps with a far smaller rounding error, used as the reference for long runs against a
  * 1e-12 bar that lies below the binary64 build's own accumulated rounding. */
 #ifdef ORC_DD
 #include "dd.hpp"

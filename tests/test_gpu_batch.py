@@ -118,7 +118,7 @@ def test_ricker_batch_from_rest_matches_oracle():
     steps = 40
     outs = _run_batch(d, m, shots, steps, True)
     for (ncell, dt, st, src), (pb, ub) in zip(shots, outs):
-        # 40 steps: judged by the oracle's double-double build (see test_gpu_parity)
+        # 40 steps: compared with the oracle's double-double build (see test_gpu_parity)
         po, uo = oracle.run_source(d, m, ncell, dt, st.p, st.u, steps, **src, prec="dd")
         assert np.abs(po).max() > 0
         assert rel_err(pb, po) <= 1e-12 and rel_err(ub, uo) <= 1e-12

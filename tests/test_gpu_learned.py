@@ -165,7 +165,7 @@ def test_features_and_targets_match_oracle():
 
 
 def _trajectory(seed, nc, r, steps):
-    """Coarse and fine solutions of one seeded pulse at the same time (fine = judge)."""
+    """Coarse and fine solutions of one seeded pulse at the same time (fine = reference)."""
     rng = np.random.default_rng(seed)
     width = float(rng.uniform(0.06, 0.12))
     nf = [nc[0] * r, nc[1] * r]

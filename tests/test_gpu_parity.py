@@ -3,10 +3,10 @@
 Bar (stated in the workload definition): per field, max |gpu - oracle| / max |oracle|
 <= 1e-12 after the run, FP64 throughout.  Summation order differs between the two
 (butterflied fused operator vs. per-axis reconstruction + series), so results agree to
-rounding, not bitwise.  Runs of 20 steps or more are judged against the oracle's
-double-double build (JUDGE): after hundreds of steps the binary64 oracle's own accumulated
+rounding, not bitwise.  Runs of 20 steps or more are compared with the oracle's
+double-double build (DD_REF): after hundreds of steps the binary64 oracle's own accumulated
 rounding (1.3e-12 on the 1000-step 1D workload, 2e-12 on the 200-step 2D one) is as
-large as the bar, so only a more precise judge can tell whether the GPU meets it.
+large as the bar, so only a more precise reference can tell whether the GPU meets it.
 """
 from __future__ import annotations
 
@@ -22,7 +22,7 @@ from paper_1808_10481_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
-JUDGE = "dd"
+DD_REF = "dd"
 EPS = np.finfo(np.float64).eps
 _ROWSUM = {}
 
@@ -118,7 +118,7 @@ def test_config1_full_1d_standing_mode():
     d, m, ncell = 1, 3, [64]
     dt = I.cfl_dt(ncell)
     st = I.standing_mode(d, m, ncell, dt, wave=[3])
-    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec=JUDGE)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 1000, prec=DD_REF)
     pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 1000)
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
     ex = I.standing_mode_exact(d, m, ncell, [3], 1000 * dt, 1000.5 * dt)
@@ -132,7 +132,7 @@ def test_config2_reduced_full_run(path):
     d, m, ncell = 2, 3, [48, 40]
     dt = I.cfl_dt(ncell)
     st = I.gaussian_pulse(d, m, ncell, dt, seed=1)
-    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 200, prec=JUDGE)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 200, prec=DD_REF)
     pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 200, path)
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
 
@@ -142,7 +142,7 @@ def test_config3_reduced_full_run():
     d, m, ncell = 3, 2, [12, 12, 12]
     dt = I.cfl_dt(ncell)
     st = I.plane_wave(m, ncell, dt, seed=3)
-    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 40, prec=JUDGE)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 40, prec=DD_REF)
     pg, ug = gpu_run(d, m, ncell, dt, st.p, st.u, 40)
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
 
@@ -292,7 +292,7 @@ def test_point_source_parity(d, m, ncell, x0, sigma):
     p = np.zeros((nnode, nq))
     u = np.zeros((d, nnode, nq))
     f0, amp, steps = 14.0, 1.0, 60
-    po, uo = oracle.run_source(d, m, ncell, dt, p, u, steps, x0, sigma, f0, amp, prec=JUDGE)
+    po, uo = oracle.run_source(d, m, ncell, dt, p, u, steps, x0, sigma, f0, amp, prec=DD_REF)
     pg, ug = gpu_run_source(d, m, ncell, dt, p, u, steps, x0, sigma, f0, amp, chunks=2)
     assert np.abs(po).max() > 0
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL

@@ -447,7 +447,7 @@ def test_source_superposition():
 
 
 def test_double_double_build_agrees_with_binary64():
-    """The double-double build (the judge of long GPU runs) is the same algorithm: on a short
+    """The double-double build (the reference of long GPU runs) is the same algorithm: on a short
     run the two builds agree to binary64 rounding, and on the 1000-step 1D workload they
     differ by no more than the binary64 build's accumulated rounding."""
     d, m, ncell = 2, 3, [12, 10]
