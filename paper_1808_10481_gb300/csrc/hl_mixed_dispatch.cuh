@@ -60,7 +60,8 @@ static cudaError_t run_mixed_t(const LaunchFp64 &a)
     k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.P, a.Ph, a.Pl, a.p_elems);
     k_shadow<COMP><<<sb, 256, 0, a.stream>>>(a.U, a.Uh, a.Ul, a.p_elems * D);
     // keep all D float-float accumulator blocks of the u-half in registers only when small
-    constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) <= 64;
+    // (2D float-float m = 3, 64 accumulators, measured 23% faster split)
+    constexpr bool fused = D * S::NQ * (COMP ? 2 : 1) < 64;
     const dim3 grid((unsigned)a.total_tiles), block((unsigned)a.tx, (unsigned)a.ty);
     const int region = region_nodes<D>(a.tx, a.ty);
     // kMixedBufs pipeline buffers of LC slots each (hi, and lo for the

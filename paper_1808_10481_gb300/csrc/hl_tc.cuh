@@ -49,6 +49,16 @@ __device__ __forceinline__ long long f32_fixed(float f, int sh)
     return (b & 0x80000000u) ? -v : v;
 }
 
+// BF16 bits of a digit d in [-128, 127] without a conversion instruction (an
+// int64 -> float conversion issues on the FP64 pipe): 1.5 * 2^23 + d is exact
+// in binary32, subtracting 1.5 * 2^23 leaves d exactly, and d has at most
+// 8 significant bits, so its binary32 bits truncate to its BF16 bits.
+__device__ __forceinline__ uint32_t bf16_of_digit(int d)
+{
+    const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
+    return __float_as_uint(f) >> 16;
+}
+
 // 2^k as a binary32 (0 below the normal range)
 __device__ __forceinline__ float pow2f(int k)
 {
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                 if (r1 >= 128) r1 -= 256;
                 X0 = (X0 - r0) >> 8;
                 X1 = (X1 - r1) >> 8;
-                As[tc_word(j * R + r, w)] = (__float_as_uint((float)r0) >> 16) | (__float_as_uint((float)r1) & 0xFFFF0000u);
+                As[tc_word(j * R + r, w)] = bf16_of_digit((int)r0) | (bf16_of_digit((int)r1) << 16);
             }
         }
         __syncthreads();
