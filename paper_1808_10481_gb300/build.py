@@ -51,10 +51,26 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libhl.so; returns its path.  Raises on any compiler error."""
+    """Compile and link libhl.so; returns its path.  Raises on any compiler error.
+
+    Processes that build at once (one per rank) serialise on a lock file, so
+    the object files are written by one of them and the others find the
+    library up to date."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build_locked(verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool) -> str:
     nvcc = _nvcc()
     procs = []
     objs = []
