@@ -66,14 +66,20 @@ __device__ __forceinline__ float pow2f(int k)
     return __uint_as_float((unsigned)(k + 127) << 23);
 }
 
-// 32-bit shared load kept in program order with the mma.sync statements (a
-// volatile asm), so the fragments of later digit pairs are not hoisted into
-// registers all at once
-__device__ __forceinline__ uint32_t lds_u32(const void *p)
+// ldmatrix: four (x4) or two (x2) 8x8 BF16 matrices from shared memory, each
+// lane giving the address of one 16-byte row; the registers come out in the
+// mma.sync fragment layout
+__device__ __forceinline__ void ldsm_x4(uint32_t *r, const void *p)
 {
-    uint32_t v;
-    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
-    return v;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t &r0, uint32_t &r1, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
 }
 
 __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, uint32_t b0, uint32_t b1)
@@ -248,8 +254,11 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
             constexpr int a = decltype(ac)::value;
             const int mt = warp + 8 * a;
             if (mt < nmt) {
-                const int q0 = mt * 16 + g, q1 = q0 + 8;  // the fragment rows' nodes in the tile
-                const int rq0 = q0 % tx + RX * (q0 / tx), rq1 = q1 % tx + RX * (q1 / tx);
+                // ldmatrix row of this lane: A rows (lane % 8) + 8 ((lane / 8) % 2) of
+                // the row block, k half lane / 16; B row lane % 8, k half (lane / 8) % 2
+                const int qa = mt * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+                const int rqa = qa % tx + RX * (qa / tx);
+                const int kha = lane >> 4, khb = (lane >> 3) & 1;
                 // one 8-column half of the outputs at a time (fewer live accumulators)
                 static_for<0, 2>([&](auto ntc) {
                     constexpr int nt = decltype(ntc)::value;
@@ -261,17 +270,17 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                     static_for<0, 4>([&](auto vc) {
                         constexpr int v = decltype(vc)::value;
                         const int dv = (v & 1) + RX * (v >> 1);
-                        const uint16_t *bcol = Bo + (size_t)(nt * 8 + g) * kTcKS + (c * 4 + v) * 16 + 2 * t;
+                        const uint16_t *bcol = Bo + (size_t)(nt * 8 + (lane & 7)) * kTcKS + (c * 4 + v) * 16 + 8 * khb;
                         static_for<0, kTcDigits>([&](auto ic) {
                             constexpr int i = decltype(ic)::value;
-                            const int ra = i * R + rq0 + dv, rb = i * R + rq1 + dv;
-                            const uint32_t af[4] = {lds_u32(As + tc_word(ra, t)), lds_u32(As + tc_word(rb, t)),
-                                                    lds_u32(As + tc_word(ra, t + 4)), lds_u32(As + tc_word(rb, t + 4))};
+                            uint32_t af[4];
+                            ldsm_x4(af, As + tc_word(i * R + rqa + dv, 4 * kha));
                             static_for<0, kTcDigits>([&](auto jc) {
                                 constexpr int j = decltype(jc)::value;
                                 if constexpr (i + j < kTcLevels) {
-                                    const uint16_t *bp = bcol + (size_t)j * kTcN * kTcKS;
-                                    mma_bf16(acc[i + j], af, lds_u32(bp), lds_u32(bp + 8));
+                                    uint32_t b0, b1;
+                                    ldsm_x2(b0, b1, bcol + (size_t)j * kTcN * kTcKS);
+                                    mma_bf16(acc[i + j], af, b0, b1);
                                 }
                             });
                         });
