@@ -149,9 +149,24 @@ def cpu_baseline_sample(target_s: float = 15.0):
     t2 = time.perf_counter() - t0
     steps = 1 + extra
     secs = t1 + t2
-    return {"value": dofs() * steps / secs, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+    cores = oracle.threads()
+    # the same oracle on one thread, on a 128^2 grid (one 512^2 step takes half a minute there)
+    n1 = [128] * DIM
+    dt1 = I.cfl_dt(n1)
+    st1 = I.gaussian_pulse(DIM, M, n1, dt1, seed=1)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.run(DIM, M, n1, dt1, st1.p, st1.u, 2)
+        s1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    dof1 = (DIM + 1) * (M + 1) ** DIM * 128 ** DIM * 2
+    return {"value": dofs() * steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} leapfrog step(s) of the 512^2 m=3 problem in {secs:.1f} s "
-                      f"(plain C oracle, OpenMP over nodes)"}
+                      f"(plain C oracle, OpenMP over nodes)",
+            "single_core": {"value": dof1 / s1, "unit": UNIT, "cores": 1,
+                            "sample": f"2 leapfrog steps of the 128^2 m=3 problem in {s1:.1f} s on one thread"}}
 
 
 def run_reference(args, rank):
