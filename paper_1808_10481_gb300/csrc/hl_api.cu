@@ -271,13 +271,13 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
             if (!h->Ul) HL_CK(h, cudaMalloc(&h->Ul, n * h->dim * sizeof(float)));
         }
     }
-    if (mode == HL_TC_SPLIT && !h->tc_digits) {
+    if (mode == HL_TC_SPLIT && (!h->tc_digits || !h->tc_expo)) {
         std::vector<uint16_t> dig;
         std::vector<int> ex;
         if (!build_tc_tables(h->m, h->coef.data(), dig, ex))
             return set_err(h, HL_EINVAL, "tensor-core tables need m <= 3");
-        HL_CK(h, cudaMalloc(&h->tc_digits, dig.size() * sizeof(uint16_t)));
-        HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
+        if (!h->tc_digits) HL_CK(h, cudaMalloc(&h->tc_digits, dig.size() * sizeof(uint16_t)));
+        if (!h->tc_expo) HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
         HL_CK(h, cudaMemcpy(h->tc_digits, dig.data(), dig.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         HL_CK(h, cudaMemcpy(h->tc_expo, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
     }

@@ -277,3 +277,31 @@ def test_tc_split_validation():
                 hl.hl_set_precision(h, hl.HL_TC_SPLIT)
         finally:
             hl.hl_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["fp32_comp", "tc_split"])
+def test_autotune_in_mixed_modes_leaves_state_untouched(mode):
+    """The autotuner times every tile shape in the handle's precision mode on scratch copies:
+    the state and the step counter are unchanged, and stepping afterwards still matches the
+    oracle within the mode's bound."""
+    prec = {"fp32_comp": hl.HL_FP32_COMP, "tc_split": hl.HL_TC_SPLIT}[mode]
+    d, m, ncell = 2, 3, [40, 36]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=91)
+    h = hl.hl_create(d, m, ncell, dt)
+    try:
+        hl.hl_set_precision(h, prec)
+        hl.hl_set_initial(h, st.p, st.u)
+        best, ms = hl.hl_autotune(h, 1)
+        assert 0 <= best < hl.HL_NUM_TILES and ms[best] > 0
+        p0, u0, _, _ = hl.hl_get_fields(h)
+        np.testing.assert_array_equal(p0, st.p.reshape(p0.shape))
+        np.testing.assert_array_equal(u0, st.u.reshape(u0.shape))
+        assert hl.hl_info(h)[2] == 0
+        hl.hl_step(h, 4)
+        pg, ug, _, _ = hl.hl_get_fields(h)
+    finally:
+        hl.hl_destroy(h)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, 4)
+    bound = tc_bound(d, m, 4) if mode == "tc_split" else 4 * EPS[2] * rowsum(d, m) * 4
+    assert max(rel_err(pg, po), rel_err(ug, uo)) <= bound

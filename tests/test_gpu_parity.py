@@ -147,12 +147,17 @@ def test_config3_reduced_full_run():
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
 
 
-def _sampled_step_parity(d, m, ncell, dt, st, warm_steps, n_sample, seed):
+def _sampled_step_parity(d, m, ncell, dt, st, warm_steps, n_sample, seed, tile="auto"):
     """At full size: run warm_steps on the GPU, read the state, do one more step on the
-    GPU and compare sampled nodes with the oracle's half-steps from the GPU state."""
+    GPU and compare sampled nodes with the oracle's half-steps from the GPU state.
+    tile "auto" runs the autotuner first, as the benchmark does; an index fixes the shape."""
     h = hl.hl_create(d, m, ncell, dt)
     try:
         hl.hl_set_initial(h, st.p, st.u)
+        if tile == "auto":
+            hl.hl_autotune(h, 2)
+        else:
+            hl.hl_set_option(h, hl.HL_OPT_TILE, tile)
         hl.hl_step(h, warm_steps)
         p0, u0, _, _ = hl.hl_get_fields(h)
         hl.hl_step(h, 1)
@@ -169,11 +174,13 @@ def _sampled_step_parity(d, m, ncell, dt, st, warm_steps, n_sample, seed):
     assert rel_err(u1[:, nodes], u_half) <= TOL
 
 
-def test_config2_full_size_sampled():
-    """512^2, m = 3: the workload and launch configuration the benchmark times."""
+@pytest.mark.parametrize("tile", ["auto", 0, 9, 12])
+def test_config2_full_size_sampled(tile):
+    """512^2, m = 3: the workload the benchmark times, in its autotuned launch configuration
+    and on the one-node, paired and p-half-paired tile shapes."""
     d, m, ncell = 2, 3, [512, 512]
     dt = I.cfl_dt(ncell)
-    _sampled_step_parity(d, m, ncell, dt, I.gaussian_pulse(d, m, ncell, dt, seed=1), 20, 4000, 5)
+    _sampled_step_parity(d, m, ncell, dt, I.gaussian_pulse(d, m, ncell, dt, seed=1), 20, 4000, 5, tile)
 
 
 def test_config3_full_size_sampled():
