@@ -371,21 +371,40 @@ def run_aux(args, rank=0, world=1, dist=None):
         n_shots = len(mine)
         cells = [[n, n] for n in sizes]
         dts = [I.cfl_dt(c) for c in cells]
-        h = hl.hl_create_batch(d, m, cells, dts)
-        hl.hl_set_stream(h, stream)
-        best, tile_ms = hl.hl_autotune(h, 2)
-        hl.hl_set_sources(h, x0, [0.01] * n_shots, f0, [1.0] * n_shots)
-        hl.hl_step(h, 5)
-        hl.hl_sync(h)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        hl.hl_step(h, lf)
-        e1.record(stream)
-        rc = hl.hl_sync(h)
-        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-        hl.hl_destroy(h)
+        def run_batch(mode):
+            h = hl.hl_create_batch(d, m, cells, dts)
+            try:
+                hl.hl_set_stream(h, stream)
+                hl.hl_set_precision(h, mode)
+                best, tile_ms = hl.hl_autotune(h, 2)
+                hl.hl_set_sources(h, x0, [0.01] * n_shots, f0, [1.0] * n_shots)
+                hl.hl_step(h, 5)
+                hl.hl_sync(h)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hl.hl_step(h, lf)
+                e1.record(stream)
+                rc = hl.hl_sync(h)
+                p_dev = torch.empty(h.nnode * h.nq, dtype=torch.float64, device="cuda")
+                hl.hl_get_fields_device(h, p_dev, None)
+            finally:
+                hl.hl_destroy(h)
+            return e0.elapsed_time(e1), rc, best, tile_ms, p_dev
+
+        ms, rc, best, tile_ms, p64 = run_batch(hl.HL_FP64)
+        ms = max_over_ranks(ms, dist, "cuda")
         nnode = sum(n * n for n in sizes_all)
         dof = (d + 1) * (m + 1) ** d * nnode
+        # the same run in the mixed modes (every shot has dt/h = 0.9, so one operator table serves all)
+        modes = {}
+        scale = float(p64.abs().max())
+        for name, mode in (("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)):
+            ms_m, rc_m, best_m, _, pm = run_batch(mode)
+            ms_m = max_over_ranks(ms_m, dist, "cuda")
+            modes[name] = {"value": dof * lf / (ms_m / 1e3), "ms_per_run": ms_m, "tile": hl.TILES[best_m],
+                           "max_rel_diff_vs_fp64_p": float((pm - p64).abs().max()) / scale if scale > 0 else 0.0,
+                           "status": rc_m}
+            del pm
         fl = fp64_flops_per_node_step(d, m) * nnode * lf
         out.update({"workload": "batch", "n_gpus": world, "scaling": "strong (64 shots split by cost)", "value": dof * lf / (ms / 1e3), "ms_per_run": ms,
                     "config": {"workload": "64 independent 2D shots, n ~ U{128..1024} per axis (seed 2024), m=3, "
@@ -395,6 +414,7 @@ def run_aux(args, rank=0, world=1, dist=None):
                     "roofline": {"bound": "alu", "achieved": fl / (ms / 1e3) / 1e12 / world,
                                  "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                                  "frac": fl / (ms / 1e3) / FP64_PEAK_FLOPS / world},
+                    "mixed_modes": modes,
                     "status": rc})
     if rank == 0:
         print(json.dumps(out), flush=True)
