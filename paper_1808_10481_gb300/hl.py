@@ -26,6 +26,7 @@ HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
 HL_NUM_TILES = 14
+HL_NOALLOC_SCRATCH_BYTES = 65536
 HL_MLP_IN, HL_MLP_HIDDEN, HL_MLP_OUT, HL_MLP_NPARAMS = 288, 128, 16, 55568
 TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16),
          (32, 4, "paired"), (32, 8, "paired"), (64, 4, "paired"), (16, 16, "paired"),

@@ -45,6 +45,19 @@ def test_binding_wraps_every_declared_symbol():
         assert callable(getattr(hl, name, None)), name
 
 
+def test_binding_constants_match_the_header():
+    """Every HL_* constant of the header (enums and #defines) has the same value in the binding,
+    and the binding's tile list has one entry per tile shape."""
+    import re
+    text = open(os.path.join(ROOT, "include", "hl.h")).read()
+    consts = {k: int(v) for k, v in re.findall(r"\b(HL_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    consts.update({k: int(v) for k, v in re.findall(r"#define\s+(HL_[A-Z0-9_]+)\s+(-?\d+)", text)})
+    assert len(consts) > 20
+    for k, v in consts.items():
+        assert getattr(hl, k) == v, k
+    assert len(hl.TILES) == hl.HL_NUM_TILES
+
+
 @pytest.mark.parametrize("args,fragment", [
     ((0, 3, [8], 0.01), "dim"),
     ((4, 3, [8], 0.01), "dim"),
