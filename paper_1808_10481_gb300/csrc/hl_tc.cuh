@@ -5,19 +5,21 @@
 // A (k = partner component, vertex, slot; 16 slots per block of k, zero
 // padded) and the vertex form of the fused operator is B[k][s] (the host's
 // digit tables, build_tc_tables).  Both operands are cut into kTcDigits
-// balanced base-256 digits after a power-of-two scaling: the block's partner
-// data by 2^-E with E from the block maximum (one E per partner component),
-// every operator column by its own 2^-e_n.  A digit product is an integer of
-// magnitude <= 2^14 and a sum of K <= 128 of them, over the <= 6 digit pairs
-// of one level, stays below 2^24, so the FP32 accumulators of mma.sync hold
-// it exactly.  Digit pairs (i, j) with i + j <= kTcLevels - 1 are formed; level
-// L = i + j carries weight 2^(E + e_n - 12 - 8 L).  The levels are summed in
+// base-256 digits after a power-of-two scaling: the block's partner data by
+// 2^-E with E from the block maximum (one E per partner component), every
+// operator column by its own 2^-e_n.  Partner digits lie in [-256, 256] (the
+// first) and [-128, 128] (the others), operator digits in [-128, 127]; the sum
+// of one level's products over a component's K = 64 terms, at most 6 digit
+// pairs of which one may hold a first partner digit, stays below
+// 64 (2^15 + 5 2^14) < 2^23, so the FP32 accumulators of mma.sync hold it
+// exactly.  Digit pairs (i, j) with i + j <= kTcLevels - 1 are formed; level
+// L = i + j carries weight 2^(E + e_n - 14 - 8 L).  The levels are summed in
 // float-float and the increment is added to the binary64 node value.
 //
 // The partner values enter as their float-float shadows (hi + lo, 48 bits);
-// quantisation to 46 bits below the block maximum and the dropped levels
-// (L >= kTcLevels) bound the error by a few 2^-46 of max|data| times the
-// operator's column sums per half-step.
+// quantisation to 48 bits below the block maximum (46 below each operator
+// column maximum) and the dropped levels (L >= kTcLevels) bound the error by a
+// few 2^-46 of max|data| times the operator's column sums per half-step.
 #pragma once
 
 #include <atomic>
@@ -226,23 +228,32 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
 #pragma unroll
         for (int w = 1; w < kTcThreads / 32; ++w) mx = fmaxf(mx, red[w]);
         const int E = mx > 0.f ? (int)((__float_as_uint(mx) >> 23) & 0xFFu) - 126 : 0;
-        // partner digits: round((hi + lo) 2^(46 - E)) in balanced base 256; a
-        // thread converts a slot pair of one region node
+        // partner digits on the FP32 pipe: with x = (hi + lo) 2^-E, |x| < 1, digit j is
+        // the nearest integer to 256 x_j and x_{j+1} = 256 x_j - d_j, the remainder
+        // kept exactly as a float-float pair; d_0 lies in [-256, 256], the others in
+        // [-128, 128], and x = sum_j d_j 256^-(j+1) to 2^-49.  A thread converts a
+        // slot pair of one region node.
         constexpr int NW = (NQ + 1) / 2;  // slot pairs; consecutive threads fill one row's words
+        const float sc = pow2f(-E);
 #pragma unroll 1
         for (int e = tid; e < NW * R; e += kTcThreads) {
             const int w = e % NW, r = e / NW, l0 = 2 * w;
-            long long X0 = f32_fixed(Fh[l0 * R + r], 46 - E) + f32_fixed(Fl[l0 * R + r], 46 - E);
-            long long X1 = 0;
-            if (l0 + 1 < NQ) X1 = f32_fixed(Fh[(l0 + 1) * R + r], 46 - E) + f32_fixed(Fl[(l0 + 1) * R + r], 46 - E);
+            float h0 = Fh[l0 * R + r] * sc, q0 = Fl[l0 * R + r] * sc, h1 = 0.f, q1 = 0.f;
+            if (l0 + 1 < NQ) {
+                h1 = Fh[(l0 + 1) * R + r] * sc;
+                q1 = Fl[(l0 + 1) * R + r] * sc;
+            }
 #pragma unroll
-            for (int j = kTcDigits - 1; j >= 0; --j) {
-                long long r0 = X0 & 255, r1 = X1 & 255;
-                if (r0 >= 128) r0 -= 256;
-                if (r1 >= 128) r1 -= 256;
-                X0 = (X0 - r0) >> 8;
-                X1 = (X1 - r1) >> 8;
-                As[tc_word(j * R + r, w)] = bf16_of_digit((int)r0) | (bf16_of_digit((int)r1) << 16);
+            for (int j = 0; j < kTcDigits; ++j) {
+                const float t0 = h0 * 256.f, t1 = h1 * 256.f;
+                // round to the nearest integer: 1.5 * 2^23 has a unit last place
+                const float d0 = __fsub_rn(__fadd_rn(t0, 12582912.f), 12582912.f);
+                const float d1 = __fsub_rn(__fadd_rn(t1, 12582912.f), 12582912.f);
+                const FF r0 = ff_two_sum(__fsub_rn(t0, d0), q0 * 256.f);
+                const FF r1 = ff_two_sum(__fsub_rn(t1, d1), q1 * 256.f);
+                h0 = r0.hi, q0 = r0.lo, h1 = r1.hi, q1 = r1.lo;
+                // an integer of at most 8 significant bits: its binary32 bits cut to BF16
+                As[tc_word(j * R + r, w)] = (__float_as_uint(d0) >> 16) | (__float_as_uint(d1) & 0xFFFF0000u);
             }
         }
         __syncthreads();
@@ -285,10 +296,11 @@ __global__ void __launch_bounds__(kTcThreads, MTW == 1 ? 2 : 1)
                             });
                         });
                     });
-                    // levels -> float-float, scaled by 2^(E + e_n - 12 - 8 L) (exact)
+                    // levels -> float-float, scaled by 2^(E + e_n - 14 - 8 L) (exact): partner
+                    // digit i weighs 2^(E - 8 - 8 i), operator digit j 2^(e_n - 6 - 8 j)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int k0 = E + en[o][nt][e & 1] - 12;
+                        const int k0 = E + en[o][nt][e & 1] - 14;
 #pragma unroll
                         for (int L = 0; L < kTcLevels; ++L) {
                             const float val = acc[L][e] * pow2f(k0 - 8 * L);
