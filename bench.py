@@ -50,7 +50,7 @@ FP64_PEAK_FLOPS = N_SM * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (keyed by the hash of the kernel header).
 # Captured on this workload (512^2, paired 32x8 tile), mean of two launches,
-# ncu's default cache flush before each launch (profiles/traffic_k_p_half_pair_2d_m3_512.md).
+# ncu's default cache flush before each launch.
 TRAFFIC_SOURCE_HASH = "5629d2e800a9a677"
 TRAFFIC_BYTES = {"p_half": 103940096, "u_half": None}
 
