@@ -242,6 +242,23 @@ def test_2d_stable_at_cfl(m):
     assert rho_bad > 1.5
 
 
+@pytest.mark.parametrize("m", [0, 1])
+def test_3d_stable_at_cfl(m):
+    """Section 5 builds the multi-dimensional scheme as a tensor product and states that
+    three dimensions follow the same construction; the 3D step at dt = 0.9 min(h) keeps its
+    spectrum in the unit disc and loses it at twice that step.  The eigenvalue 1 of the
+    periodic step is defective: derivative data can be periodic while the field they
+    describe is not (a constant slope of p drives a velocity that grows linearly in time),
+    and such modes grow polynomially.  Rounding moves a defective eigenvalue by about
+    eps^(1/3), so the bound carries that margin."""
+    ncell = [2, 3, 2]                # three different h
+    dt = 0.9 * min(1.0 / n for n in ncell)
+    rho = np.abs(np.linalg.eigvals(_step_matrix(3, m, ncell, dt))).max()
+    assert rho <= 1.0 + 1e-5
+    rho_bad = np.abs(np.linalg.eigvals(_step_matrix(3, m, ncell, 2.0 * dt))).max()
+    assert rho_bad > 1.5
+
+
 # ----------------------------------------------------------------------------- conservation
 def _piecewise(data, m, h, offset):
     """Independent piecewise interpolant of node data (N, m+1) on the periodic unit line.
