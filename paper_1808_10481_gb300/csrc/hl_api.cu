@@ -565,14 +565,25 @@ extern "C" int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile
     int rc = check_usable(h);
     if (rc) return rc;
     if (steps_per_trial < 1) return set_err(h, HL_EINVAL, "steps_per_trial must be >= 1");
-    // trials run on scratch copies of the state, so the solution is not advanced
-    double *sp = nullptr, *su = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // trials run on scratch copies of the state, so the solution is not advanced;
+    // the scratch is released on every return (cudaFree waits for the trials)
+    struct Scratch {
+        double *sp = nullptr, *su = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Scratch()
+        {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            if (sp) cudaFree(sp);
+            if (su) cudaFree(su);
+        }
+    } scr;
+    double *&sp = scr.sp, *&su = scr.su;
+    cudaEvent_t &e0 = scr.e0, &e1 = scr.e1;
     const size_t pb = (size_t)h->p_elems * sizeof(double);
     HL_CK(h, cudaStreamSynchronize(h->stream));
     cudaError_t e;
     if ((e = cudaMalloc(&sp, pb)) != cudaSuccess || (e = cudaMalloc(&su, pb * h->dim)) != cudaSuccess) {
-        if (sp) cudaFree(sp);
         cudaGetLastError();
         return set_err(h, HL_ENOMEM, std::string("autotune scratch: ") + cudaGetErrorString(e));
     }
@@ -607,10 +618,6 @@ extern "C" int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile
     }
     HL_CK(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));  // trial data may be anything
     HL_CK(h, cudaStreamSynchronize(h->stream));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(sp);
-    cudaFree(su);
     if (rc) {
         build_tiles(h, keep_tile);
         return rc;
