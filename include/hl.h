@@ -123,6 +123,24 @@ int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out
 int hl_create_batch(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out);
 
 /*
+ * hl_create_spacing -- hl_create for a periodic grid whose node spacing is
+ * not 1/n_cells[k]: n_cells[k] nodes spaced h_k = 1/inv_h[k] apart, period
+ * n_cells[k]/inv_h[k] along axis k.  The update's Courant parameter is
+ * lam_k = dt*inv_h[k]/2 = dt/(2 h_k) (Section 2: the interpolant lives on a
+ * cell of width h and is evolved over dt/2), so hl_create(dim, m, n, dt) is
+ * hl_create_spacing with inv_h = n, bit for bit.
+ *   inv_h : dim entries, finite and > 0.
+ *   dt    : 0 < dt < min_k h_k.
+ * Its use is the slab of a larger grid: a process that owns L planes of an
+ * axis of N nodes creates L + 2 planes with inv_h = N along that axis, the
+ * outer two being ghost copies of its neighbours' edge planes, refreshed
+ * before every step.  Point sources and the learned-correction calls assume
+ * the unit box and reject a handle whose inv_h differs from n_cells
+ * (HL_EINVAL).  Other validation and error codes as hl_create.
+ */
+int hl_create_spacing(int dim, int m, const int64_t *n_cells, const double *inv_h, double dt, hl_solver **out);
+
+/*
  * hl_set_initial -- copy host initial data (host layout) to the device.
  *   p : prod(n_cells)*nq doubles, p at t = 0.
  *   u : dim*prod(n_cells)*nq doubles, u at t = dt/2.

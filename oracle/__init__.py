@@ -139,9 +139,12 @@ def _out(a: np.ndarray, raw: bool = False):
     return a
 
 
-def lambdas(ncell, dt: float, prec: str = "f64") -> np.ndarray:
-    """lam_k = dt / (2 h_k) with h_k = 1/ncell_k (periodic unit box), computed in binary64."""
-    lam = np.array([dt * n / 2.0 for n in ncell] + [0.0] * (3 - len(ncell)), dtype=np.float64)
+def lambdas(ncell, dt: float, prec: str = "f64", inv_h=None) -> np.ndarray:
+    """lam_k = dt / (2 h_k), computed in binary64 as dt * (1/h_k) / 2.  By default
+    h_k = 1/ncell_k (periodic unit box); inv_h gives 1/h_k explicitly (a grid of
+    ncell_k nodes spaced h_k apart, e.g. one slab of a larger grid)."""
+    inv = list(ncell) if inv_h is None else list(inv_h)
+    lam = np.array([dt * float(n) / 2.0 for n in inv] + [0.0] * (3 - len(inv)), dtype=np.float64)
     return _arr(lam, prec)
 
 
@@ -198,16 +201,16 @@ def half_step_nodes(d: int, m: int, ncell, dt: float, mode: int, src: np.ndarray
 
 
 def run(d: int, m: int, ncell, dt: float, p: np.ndarray, u: np.ndarray, n_steps: int, prec: str = "f64",
-        raw: bool = False):
+        raw: bool = False, inv_h=None):
     """n_steps leapfrog steps; returns new (p, u) arrays (inputs untouched).
 
     p has shape (nnode, nq), u (d, nnode, nq); node index x-fastest,
-    slot q = a_0 + (m+1)(a_1 + (m+1) a_2)."""
+    slot q = a_0 + (m+1)(a_1 + (m+1) a_2).  inv_h: see lambdas()."""
     lib = _load(prec)
     p = _arr(p, prec, copy=True)
     u = _arr(u, prec, copy=True)
-    lib.oracle_run(d, m, _i64p(_nc(ncell)), _ptr(lambdas(ncell, dt, prec)), _ptr(_h_array(m, prec)), _ptr(p),
-                   _ptr(u), int(n_steps))
+    lib.oracle_run(d, m, _i64p(_nc(ncell)), _ptr(lambdas(ncell, dt, prec, inv_h)), _ptr(_h_array(m, prec)),
+                   _ptr(p), _ptr(u), int(n_steps))
     return _out(p, raw), _out(u, raw)
 
 

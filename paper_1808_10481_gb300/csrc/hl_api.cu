@@ -117,7 +117,9 @@ static int build_tiles(hl_solver *h, int tile)
     return HL_OK;
 }
 
-static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out)
+// inv_h: per-shot node spacings as 1/h_k (NULL: the unit box, h_k = 1/n_cells[k])
+static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, const double *inv_h, const double *dt,
+                         hl_solver **out)
 {
     if (out) *out = nullptr;
     if (!out) return set_err(nullptr, HL_EINVAL, "out is NULL");
@@ -131,9 +133,11 @@ static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, co
     int64_t nq = 1;
     for (int k = 0; k < dim; ++k) nq *= (m + 1);
     int64_t p_elems = 0;
+    bool unit_box = true;
     for (int s = 0; s < n_shots; ++s) {
         Shot &sh = shots[s];
-        double hmin = 1.0;
+        double hmin = HUGE_VAL;
+        double inv[3] = {1.0, 1.0, 1.0};
         sh.nnode = 1;
         for (int k = 0; k < dim; ++k) {
             const int64_t nk = n_cells[(size_t)s * dim + k];
@@ -142,12 +146,15 @@ static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, co
             sh.n[k] = nk;
             sh.nnode *= nk;
             if (sh.nnode >= (int64_t(1) << 31)) return set_err(nullptr, HL_EINVAL, "more than 2^31-1 nodes per grid");
-            hmin = std::fmin(hmin, 1.0 / (double)nk);
+            inv[k] = inv_h ? inv_h[(size_t)s * dim + k] : (double)nk;
+            if (!(inv[k] > 0.0) || !std::isfinite(inv[k])) return set_err(nullptr, HL_EINVAL, "inv_h must be finite and > 0");
+            if (inv[k] != (double)nk) unit_box = false;
+            hmin = std::fmin(hmin, 1.0 / inv[k]);
         }
         if (!(dt[s] > 0.0) || !std::isfinite(dt[s])) return set_err(nullptr, HL_EINVAL, "dt must be finite and > 0");
         if (!(dt[s] < hmin)) return set_err(nullptr, HL_EINVAL, "dt must be below min h (c dt/dx < 1)");
         sh.dt = dt[s];
-        for (int k = 0; k < dim; ++k) sh.lam[k] = dt[s] * (double)sh.n[k] / 2.0;
+        for (int k = 0; k < dim; ++k) sh.lam[k] = dt[s] * inv[k] / 2.0;
         sh.p_off = p_elems;
         sh.u_off = p_elems * dim;
         p_elems += sh.nnode * nq;
@@ -162,6 +169,7 @@ static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, co
     h->p_elems = p_elems;
     h->u_elems = p_elems * dim;
     h->per_shot_coef = n_shots > 1;
+    h->unit_box = unit_box;
     h->use_graph = n_shots > 1;
     for (int s = 0; s < n_shots; ++s) {
         std::vector<double> c;
@@ -208,12 +216,22 @@ static int create_common(int dim, int m, int n_shots, const int64_t *n_cells, co
 
 extern "C" int hl_create(int dim, int m, const int64_t *n_cells, double dt, hl_solver **out)
 {
-    return create_common(dim, m, 1, n_cells, &dt, out);
+    return create_common(dim, m, 1, n_cells, nullptr, &dt, out);
+}
+
+extern "C" int hl_create_spacing(int dim, int m, const int64_t *n_cells, const double *inv_h, double dt,
+                                 hl_solver **out)
+{
+    if (!inv_h) {
+        if (out) *out = nullptr;
+        return set_err(nullptr, HL_EINVAL, "inv_h is NULL");
+    }
+    return create_common(dim, m, 1, n_cells, inv_h, &dt, out);
 }
 
 extern "C" int hl_create_batch(int dim, int m, int n_shots, const int64_t *n_cells, const double *dt, hl_solver **out)
 {
-    return create_common(dim, m, n_shots, n_cells, dt, out);
+    return create_common(dim, m, n_shots, n_cells, nullptr, dt, out);
 }
 
 extern "C" void hl_destroy(hl_solver *h)
@@ -635,6 +653,7 @@ extern "C" int hl_set_sources(hl_solver *h, const double *x0, const double *sigm
     int rc = check_usable(h);
     if (rc) return rc;
     if (!x0 || !sigma || !f0 || !amp) return set_err(h, HL_EINVAL, "NULL source argument");
+    if (!h->unit_box) return set_err(h, HL_EINVAL, "point sources need a unit-box handle (inv_h = n_cells)");
     const int ns = (int)h->shots.size();
     for (int s = 0; s < ns; ++s) {
         if (amp[s] == 0.0) continue;

@@ -665,6 +665,7 @@ static int solver_ok(const hl_solver *s)
     if (s->poisoned) return mlp_err(nullptr, HL_ESTATE, "solver handle poisoned");
     if (s->dim != 2 || s->m != 3 || s->shots.size() != 1)
         return mlp_err(nullptr, HL_EINVAL, "the learned correction needs a single 2D m = 3 grid");
+    if (!s->unit_box) return mlp_err(nullptr, HL_EINVAL, "the learned correction needs a unit-box grid");
     return HL_OK;
 }
 

@@ -46,6 +46,7 @@ struct hl_solver {
     std::vector<double> coef;                   // n_shots dense tables (shot 0 first)
     double *coef_dev = nullptr;
     bool per_shot_coef = false;
+    bool unit_box = true;                       // h_k = 1/n_k on every axis (hl_create_spacing may differ)
     // tiles
     int tile = 0;
     std::vector<hl::ShotDesc> shot_desc;

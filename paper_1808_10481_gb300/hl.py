@@ -51,6 +51,8 @@ _SIGNATURES = [
     ("hl_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, ctypes.POINTER(_P)]),
     ("hl_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64),
                                         ctypes.POINTER(_D), ctypes.POINTER(_P)]),
+    ("hl_create_spacing", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_D),
+                                          _D, ctypes.POINTER(_P)]),
     ("hl_set_initial", ctypes.c_int, [_P, _P, _P]),
     ("hl_set_initial_device", ctypes.c_int, [_P, _P, _P]),
     ("hl_get_fields_device", ctypes.c_int, [_P, _P, _P]),
@@ -166,6 +168,20 @@ def hl_create(dim: int, m: int, n_cells, dt: float) -> Handle:
     nc = (_I64 * len(n_cells))(*[int(x) for x in n_cells])
     out = _P()
     rc = lib.hl_create(int(dim), int(m), nc, float(dt), ctypes.byref(out))
+    if rc != HL_OK:
+        raise HLError(rc, lib.hl_last_error(None).decode(errors="replace"))
+    return Handle(out, int(dim), int(m), tuple(int(x) for x in n_cells), float(dt))
+
+
+def hl_create_spacing(dim: int, m: int, n_cells, inv_h, dt: float) -> Handle:
+    """inv_h: dim entries, 1/h_k (nodes per unit length) of a periodic grid of n_cells nodes."""
+    lib = load()
+    if len(n_cells) != dim or len(inv_h) != dim:
+        raise ValueError("n_cells and inv_h must hold dim entries")
+    nc = (_I64 * dim)(*[int(x) for x in n_cells])
+    ih = (_D * dim)(*[float(x) for x in inv_h])
+    out = _P()
+    rc = lib.hl_create_spacing(int(dim), int(m), nc, ih, float(dt), ctypes.byref(out))
     if rc != HL_OK:
         raise HLError(rc, lib.hl_last_error(None).decode(errors="replace"))
     return Handle(out, int(dim), int(m), tuple(int(x) for x in n_cells), float(dt))

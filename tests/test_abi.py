@@ -109,6 +109,33 @@ def test_kernel_sparsity_rule_matches_operator(d, m):
 
 
 @pytest.mark.parametrize("args,fragment", [
+    ((2, 3, [8, 8], [8.0, 0.0], 0.01), "inv_h"),
+    ((2, 3, [8, 8], [8.0, -4.0], 0.01), "inv_h"),
+    ((2, 3, [8, 8], [float("inf"), 8.0], 0.01), "inv_h"),
+    ((2, 3, [8, 8], [float("nan"), 8.0], 0.01), "inv_h"),
+    ((2, 3, [8, 4], [8.0, 32.0], 0.05), "min h"),      # h_y = 1/32, not 1/4
+    ((2, 3, [8, 1], [8.0, 8.0], 0.01), ">= 2"),
+])
+def test_spacing_arguments_rejected_before_cuda(args, fragment):
+    hl.load()
+    with pytest.raises(hl.HLError) as ei:
+        hl.hl_create_spacing(*args)
+    assert ei.value.code == hl.HL_EINVAL
+    assert fragment in str(ei.value)
+
+
+def test_spacing_null_inv_h_rejected(lib):
+    import ctypes
+    out = ctypes.c_void_p(1)
+    nc = (ctypes.c_int64 * 2)(8, 8)
+    fn = lib.hl_create_spacing
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    assert fn(2, 3, nc, None, 0.01, ctypes.byref(out)) == hl.HL_EINVAL
+    assert out.value is None
+    assert "inv_h" in hl.load().hl_last_error(None).decode()
+
+
+@pytest.mark.parametrize("args,fragment", [
     ((2, 3, 0, [], []), "n_shots"),
     ((2, 3, 257, [[8, 8]] * 257, [0.01] * 257), "n_shots"),
     ((2, 4, 2, [[8, 8], [8, 8]], [0.01, 0.01]), "m <= 3"),
