@@ -15,7 +15,7 @@ that share nothing with the oracle's own arithmetic.
   piecewise interpolant.
 * Section 3 (the CFL remark after eq. (vh1evolve)): stable for c dt/dx < 1, unstable
   well above it.
-* Tables 1 and 5: observed L2 convergence rates at C_CFL = 0.9.
+* Tables 1 and 5: observed L2 convergence rates at C_CFL = 0.9 and 0.5 (and 0.1 in 1D).
 """
 from __future__ import annotations
 
@@ -353,12 +353,12 @@ def test_1d_conservation_detects_wrong_step():
 
 
 # ----------------------------------------------------------------------------- convergence rates
-def _rate(d, m, Ns, T, wave):
+def _rate(d, m, Ns, T, wave, cfl=0.9):
     errs = []
     for N in Ns:
         ncell = [N] * d
         h = 1.0 / N
-        n = math.ceil(T / (0.9 * h))
+        n = math.ceil(T / (cfl * h))
         dt = T / n
         st = I.standing_mode(d, m, ncell, dt, wave=wave)
         p, u = oracle.run(d, m, ncell, dt, st.p, st.u, n)
@@ -376,21 +376,24 @@ def _check_rate(m, got, paper):
         assert 2 * m - 0.5 <= got <= 2 * m + 3.5, (m, got, paper)
 
 
+@pytest.mark.parametrize("cfl,table", [(0.9, "table1_rates_cfl09.txt"), (0.5, "table1_rates_cfl05.txt"),
+                                       (0.1, "table1_rates_cfl01.txt")])
 @pytest.mark.parametrize("m", range(0, 4))
-def test_1d_convergence_rate_matches_table1(m):
-    paper = _read_rates("table1_rates_cfl09.txt")[m]
+def test_1d_convergence_rate_matches_table1(m, cfl, table):
+    paper = _read_rates(table)[m]
     # the paper's [-1,1] standing wave sin(2 pi x) cos(2 pi t), T = 4.13, mapped to [0,1]
-    got = _rate(1, m, [16, 24, 32, 48, 64, 96], T=4.13 / 2, wave=[2])
+    got = _rate(1, m, [16, 24, 32, 48, 64, 96], T=4.13 / 2, wave=[2], cfl=cfl)
     _check_rate(m, got, paper)
     if m in (0, 2):
         assert abs(got - paper) <= 0.35
 
 
+@pytest.mark.parametrize("cfl,table", [(0.9, "table5_rates_cfl09.txt"), (0.5, "table5_rates_cfl05.txt")])
 @pytest.mark.parametrize("m", range(0, 4))
-def test_2d_convergence_rate_matches_table5(m):
-    paper = _read_rates("table5_rates_cfl09.txt")[m]
+def test_2d_convergence_rate_matches_table5(m, cfl, table):
+    paper = _read_rates(table)[m]
     # the paper's [-1,1]^2 mode sin(pi x) sin(pi y) cos(sqrt(2) pi t) mapped to [0,1]^2
-    got = _rate(2, m, [8, 12, 16, 24, 32], T=0.5, wave=[1, 1])
+    got = _rate(2, m, [8, 12, 16, 24, 32], T=0.5, wave=[1, 1], cfl=cfl)
     _check_rate(m, got, paper)
 
 
