@@ -198,3 +198,14 @@ def test_operator_table_is_correctly_rounded(d, m):
     want = _exact_operator(d, m, lam)
     ulp = np.spacing(np.abs(want))
     assert np.all(np.abs(got - want) <= ulp + 1e-300)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: a missing libhl.so is an ImportError, not a silent substitute."""
+    saved = hl._lib
+    hl._lib = None
+    try:
+        with pytest.raises(ImportError):
+            hl.load(str(tmp_path / "libhl.so"))
+    finally:
+        hl._lib = saved
