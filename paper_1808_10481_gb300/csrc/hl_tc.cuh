@@ -31,36 +31,6 @@ namespace hl {
 constexpr int kTcLevels = 7;     // digit pairs with i + j <= 6
 constexpr int kTcThreads = 256;  // 8 warps; warp w owns the 16-node row blocks w (and w + 8)
 
-
-// round(f * 2^sh) as an integer, for a binary32 f with |f * 2^sh| < 2^47
-// (integer operations; subnormals flush to zero)
-__device__ __forceinline__ long long f32_fixed(float f, int sh)
-{
-    const unsigned b = __float_as_uint(f);
-    const int e8 = (int)((b >> 23) & 0xFFu);
-    if (e8 == 0) return 0;
-    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);  // |f| = m * 2^(e8 - 150)
-    const int s = e8 - 150 + sh;
-    long long v;
-    if (s >= 0)
-        v = m << s;
-    else if (s > -40)
-        v = (m + (1ll << (-s - 1))) >> (-s);  // round half away from zero (on the magnitude)
-    else
-        v = 0;
-    return (b & 0x80000000u) ? -v : v;
-}
-
-// BF16 bits of a digit d in [-128, 127] without a conversion instruction (an
-// int64 -> float conversion issues on the FP64 pipe): 1.5 * 2^23 + d is exact
-// in binary32, subtracting 1.5 * 2^23 leaves d exactly, and d has at most
-// 8 significant bits, so its binary32 bits truncate to its BF16 bits.
-__device__ __forceinline__ uint32_t bf16_of_digit(int d)
-{
-    const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
-    return __float_as_uint(f) >> 16;
-}
-
 // 2^k as a binary32 (0 below the normal range)
 __device__ __forceinline__ float pow2f(int k)
 {
