@@ -321,3 +321,28 @@ def test_walled_solver_on_the_gpu_matches_the_doubled_box(dim, walls, m, ncell):
         s.close()
     assert _rel(got_p, ref_p) <= 1e-12
     assert _rel(got_u, ref_u) <= 1e-12
+
+
+@pytest.mark.parametrize("kind,sign", [("dirichlet", -1.0), ("neumann", 1.0)])
+def test_pulse_reflects_with_the_walls_sign(kind, sign):
+    """A right-moving pressure pulse (p = u = g(x - t)) in the walled box [0, 1/2] returns
+    from the wall at x = 1/2 inverted by a pressure-release wall and upright from a rigid
+    one (the reflection the paper's walled pulse experiment shows in 2D): at t = 1/2 the
+    pulse is back at its start, moving left, with p = sign * g."""
+    m, N = 3, 64
+    ncell, walls = [N], [kind]
+    nd = _doubled(ncell, walls)
+    h = 1.0 / nd[0]
+    x0, w = 0.25, 0.03
+    dt = 0.9 * h
+    n = math.ceil(0.5 / dt)
+    dt = 0.5 / n
+    xp = I.node_coords(nd[0], False)[: N + 1]
+    xu = I.node_coords(nd[0], True)[:N]
+    p = I.scaled_gauss(xp, h, m, x0, w, images=(0,))
+    u = I.scaled_gauss(xu, h, m, x0 + 0.5 * dt, w, images=(0,))[None]
+    got_p, _ = _walled_oracle_run(1, m, ncell, dt, walls, p, u, n)
+    want = sign * I.scaled_gauss(xp, h, m, x0, w, images=(0,))[:, 0]
+    assert np.abs(got_p[:, 0] - want).max() < 1e-3
+    if kind == "dirichlet":
+        assert abs(got_p[0, 0]) < 1e-12 and abs(got_p[N, 0]) < 1e-12
