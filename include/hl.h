@@ -297,6 +297,28 @@ int hl_kernel_times(hl_solver *h, double *ms, int64_t *launches);
 int hl_operator_table(int dim, int m, const double *lam, double *out);
 
 /*
+ * hl_tc_tables -- the operator digit tables of the tensor-core split mode
+ * (HL_TC_SPLIT, dim = 2), for inspection (host only, no CUDA call).
+ *   m      : 0..3;  lam : 2 entries, dt/(2 h_k).
+ *   digits : HL_TC_TABLE_ELEMS uint16 (BF16 bit patterns of small integers).
+ *            Entry (op, j, s, k) at ((op*6 + j)*16 + s)*136 + k: digit j
+ *            (most significant first) of row k of output column s of
+ *            operator op.  op 0 is the p-half (rows k = (c*4 + v)*16 + l:
+ *            velocity component c, cell vertex v, slot l); ops 1 and 2 are
+ *            the u-half for directions 0 and 1 (rows k = v*16 + l of p).
+ *            Vertex v has bit k set for the upper vertex along axis k; rows
+ *            and columns beyond the (m+1)^2 slots, and k >= 128, are zero.
+ *   expo   : HL_TC_EXPO_ELEMS ints, e(op, s) at op*16 + s.
+ * The operator entry is (sum_j digit_j 256^(5-j)) 2^(e - 46): the vertex form
+ * of the fused operator (the increment of output slot s per unit of the
+ * partner's slot l at vertex v), rounded to 46 bits below its column's
+ * maximum (an Ozaki-type exact split: every digit product is exact in FP32).
+ */
+#define HL_TC_TABLE_ELEMS 39168
+#define HL_TC_EXPO_ELEMS 48
+int hl_tc_tables(int m, const double *lam, uint16_t *digits, int *expo);
+
+/*
  * hl_op_counts -- floating-point work of the FP64 kernels per node and full
  * step for (dim, m): multiply-adds (one multiply-add = 2 flops) and plain
  * additions of the vertex butterflies.  Used for roofline accounting.

@@ -752,6 +752,22 @@ extern "C" int hl_operator_table(int dim, int m, const double *lam, double *out)
     return HL_OK;
 }
 
+extern "C" int hl_tc_tables(int m, const double *lam, uint16_t *digits, int *expo)
+{
+    if (m < 0 || m > 3 || !lam || !digits || !expo) return set_err(nullptr, HL_EINVAL, "bad arguments");
+    static_assert(HL_TC_TABLE_ELEMS == kTcOps * kTcOpElems && HL_TC_EXPO_ELEMS == kTcOps * kTcN,
+                  "tensor-core table sizes and header disagree");
+    const double l3[3] = {lam[0], lam[1], 0.0};
+    std::vector<double> c;
+    if (!build_operator(2, m, l3, c)) return set_err(nullptr, HL_EINVAL, "operator construction failed");
+    std::vector<uint16_t> dig;
+    std::vector<int> ex;
+    if (!build_tc_tables(m, c.data(), dig, ex)) return set_err(nullptr, HL_EINVAL, "tensor-core tables need m <= 3");
+    std::memcpy(digits, dig.data(), dig.size() * sizeof(uint16_t));
+    std::memcpy(expo, ex.data(), ex.size() * sizeof(int));
+    return HL_OK;
+}
+
 extern "C" int hl_op_counts(int dim, int m, double *fma_per_node_step, double *add_per_node_step)
 {
     if (dim < 1 || dim > 3 || m < 0 || m > 6) return set_err(nullptr, HL_EINVAL, "dim/m out of range");

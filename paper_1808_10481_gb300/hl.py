@@ -27,6 +27,7 @@ HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
 HL_NUM_TILES = 14
 HL_NOALLOC_SCRATCH_BYTES = 65536
+HL_TC_TABLE_ELEMS, HL_TC_EXPO_ELEMS = 39168, 48
 HL_MLP_IN, HL_MLP_HIDDEN, HL_MLP_OUT, HL_MLP_NPARAMS = 288, 128, 16, 55568
 TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16),
          (32, 4, "paired"), (32, 8, "paired"), (64, 4, "paired"), (16, 16, "paired"),
@@ -71,6 +72,7 @@ _SIGNATURES = [
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("hl_tc_tables", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), _P, _P]),
     ("hl_mlp_create", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_P)]),
     ("hl_mlp_destroy", None, [_P]),
     ("hl_mlp_last_error", ctypes.c_char_p, [_P]),
@@ -314,6 +316,18 @@ def hl_operator_table(dim: int, m: int, lam) -> np.ndarray:
     if rc != HL_OK:
         raise HLError(rc, hl_last_error(None))
     return out.reshape(dim, nq, nq)
+
+
+def hl_tc_tables(m: int, lam):
+    """The tensor-core split mode's operator digits (3, 6, 16, 136) as BF16 bit patterns
+    (uint16) and column exponents (3, 16)."""
+    digits = np.zeros(HL_TC_TABLE_ELEMS, dtype=np.uint16)
+    expo = np.zeros(HL_TC_EXPO_ELEMS, dtype=np.int32)
+    lm = (_D * 2)(*[float(x) for x in lam[:2]])
+    rc = load().hl_tc_tables(int(m), lm, ctypes.c_void_p(digits.ctypes.data), ctypes.c_void_p(expo.ctypes.data))
+    if rc != HL_OK:
+        raise HLError(rc, hl_last_error(None))
+    return digits.reshape(3, 6, 16, 136), expo.reshape(3, 16)
 
 
 def hl_step_noalloc(dim: int, m: int, n_cells, dt: float, p_dev, u_dev, n_steps: int, stream=None) -> int:
