@@ -66,7 +66,9 @@ enum {
     HL_EINVAL = -1,      /* invalid argument                                   */
     HL_ENOMEM = -2,      /* device or host allocation failed                   */
     HL_ECUDA = -3,       /* a CUDA call failed (handle poisoned)               */
-    HL_ETIMEOUT = -4,    /* a bounded device wait expired (handle poisoned)    */
+    HL_ETIMEOUT = -4,    /* a bounded device wait expired (handle poisoned);
+                            reserved: no kernel here waits on another launch
+                            or on the host, so no call returns it today       */
     HL_ENONFINITE = -5,  /* a NaN or Inf appeared in the updated node data     */
     HL_ESTATE = -6       /* call not valid in the handle's state               */
 };
