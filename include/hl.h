@@ -257,7 +257,7 @@ enum {
     HL_OPT_GRAPH = 3,        /* 1 = capture each hl_step call (all its launches)
                                 as one CUDA graph and launch that; default 1 for
                                 batched handles, 0 otherwise                  */
-    HL_OPT_TILE = 4          /* thread-block tile shape index 0..HL_NUM_TILES-1
+    HL_OPT_TILE = 4,         /* thread-block tile shape index 0..HL_NUM_TILES-1
                                 (nodes per block along x and y: 128x1, 256x1,
                                 64x2, 32x4, 32x8, 64x4, 16x8, 16x16; then the
                                 paired shapes 32x4, 32x8, 64x4, 16x16 whose
@@ -266,14 +266,19 @@ enum {
                                 32x8, 64x4 paired in the p-half only; dim = 1
                                 folds the tile into x and never pairs);
                                 hl_autotune picks one                          */
+    HL_OPT_STEP = 5          /* set the step counter n (>= 0) that places the
+                                state in time (p at n dt, u at (n + 1/2) dt) and
+                                clocks the point sources; hl_set_initial resets
+                                it to 0, so a run resumed from a checkpoint
+                                sets it back to the checkpoint's step count    */
 };
 
 #define HL_NUM_TILES 14
 
 /*
  * hl_set_option -- set an execution option (see the HL_OPT_* values).
- * Returns HL_EINVAL for an unknown option or value.  Options change how the
- * work is scheduled, never what is computed.
+ * Returns HL_EINVAL for an unknown option or value.  Options other than
+ * HL_OPT_STEP change how the work is scheduled, never what is computed.
  */
 int hl_set_option(hl_solver *h, int option, int64_t value);
 

@@ -328,6 +328,10 @@ extern "C" int hl_set_option(hl_solver *h, int option, int64_t value)
     case HL_OPT_TILE:
         if (value < 0 || value >= kNumTiles) return set_err(h, HL_EINVAL, "tile index out of range");
         return build_tiles(h, (int)value);
+    case HL_OPT_STEP:
+        if (value < 0) return set_err(h, HL_EINVAL, "step counter must be >= 0");
+        h->steps = value;  // read when the next hl_step is issued (source clock, field times)
+        return HL_OK;
     default:
         return set_err(h, HL_EINVAL, "unknown option");
     }

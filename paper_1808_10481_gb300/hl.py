@@ -25,6 +25,7 @@ HL_OPT_KERNEL_PATH = 1
 HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
+HL_OPT_STEP = 5
 HL_NUM_TILES = 14
 HL_NOALLOC_SCRATCH_BYTES = 65536
 HL_TC_TABLE_ELEMS, HL_TC_EXPO_ELEMS = 39168, 48

@@ -209,6 +209,37 @@ def test_checkpoint_resume_is_bitwise():
     np.testing.assert_array_equal(ua, uc)
 
 
+def test_checkpoint_resume_with_a_source_is_bitwise():
+    """A source-driven run resumed from a checkpoint (the fields, then HL_OPT_STEP back to
+    the checkpoint's step count) equals the uninterrupted run bit for bit: the source clock
+    continues from the counter.  Resuming with the counter left at 0 restarts the wavelet
+    and must differ."""
+    d, m, ncell = 2, 3, [40, 24]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=6)
+
+    def run(p, u, n, step0):
+        h = hl.hl_create(d, m, ncell, dt)
+        try:
+            hl.hl_set_initial(h, np.ascontiguousarray(p), np.ascontiguousarray(u))
+            hl.hl_set_source(h, [0.4, 0.6], 0.01, 12.0, 1.0)
+            if step0:
+                hl.hl_set_option(h, hl.HL_OPT_STEP, step0)
+            hl.hl_step(h, n)
+            return hl.hl_get_fields(h)
+        finally:
+            hl.hl_destroy(h)
+
+    pa, ua, tpa, tua = run(st.p, st.u, 30, 0)
+    pb, ub, _, _ = run(st.p, st.u, 12, 0)
+    pc, uc, tpc, tuc = run(pb, ub, 18, 12)
+    np.testing.assert_array_equal(pa, pc)
+    np.testing.assert_array_equal(ua, uc)
+    assert (tpa, tua) == (tpc, tuc)
+    pd, _, _, _ = run(pb, ub, 18, 0)
+    assert not np.array_equal(pd, pa)
+
+
 def test_deterministic():
     d, m, ncell = 3, 2, [10, 9, 8]
     dt = I.cfl_dt(ncell)
