@@ -166,3 +166,15 @@ def test_two_gloo_ranks_equal_the_undivided_grid(d, m, ncell):
     ref_p, ref_u = oracle.run(d, m, ncell, I.cfl_dt(ncell), p0, u0, steps)
     np.testing.assert_array_equal(np.concatenate([r[1] for r in results], axis=0), ref_p)
     np.testing.assert_array_equal(np.concatenate([r[2] for r in results], axis=1), ref_u)
+
+
+def test_extract_and_owned_work_on_torch_tensors():
+    torch = pytest.importorskip("torch")
+    d, m, ncell = 3, 1, [3, 2, 5]
+    nq = (m + 1) ** d
+    u = np.random.default_rng(9).standard_normal((d, 30, nq))
+    for pl in halo.slab_planes(ncell[-1], 2):
+        want = halo.extract(u, ncell, nq, d, pl)
+        got = halo.extract(torch.from_numpy(u), ncell, nq, d, pl)
+        np.testing.assert_array_equal(got.numpy(), want)
+        np.testing.assert_array_equal(halo.owned(got, ncell, nq, d, pl).numpy(), halo.owned(want, ncell, nq, d, pl))
