@@ -1,7 +1,7 @@
 """Slab decomposition with ghost-plane exchange, checked on the CPU with the oracle as the
 per-rank stepper: slabs stepped one step at a time with their ghosts refreshed in between
 must reproduce the undivided grid bit for bit (every owned node sees the same operands), in
-one process (1 to 4 slabs, ragged plane counts) and over two gloo ranks."""
+one process (1 to 4 slabs, ragged plane counts) and over two or three gloo ranks."""
 from __future__ import annotations
 
 import os
@@ -149,9 +149,11 @@ def _worker(rank, world, port, d, m, ncell, steps, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("d,m,ncell", [(2, 3, [6, 9]), (3, 1, [3, 4, 5])])
-def test_two_gloo_ranks_equal_the_undivided_grid(d, m, ncell):
-    world, steps = 2, 4
+@pytest.mark.parametrize("d,m,ncell,world", [(2, 3, [6, 9], 2), (3, 1, [3, 4, 5], 2), (2, 2, [5, 7], 3)])
+def test_gloo_ranks_equal_the_undivided_grid(d, m, ncell, world):
+    """Two ranks are each other's upper and lower neighbour (the tags keep the messages
+    apart); three ranks have distinct neighbours."""
+    steps = 4
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
