@@ -201,9 +201,11 @@ class SlabSolver:
         self.hl.hl_set_initial(self.h, p.reshape(-1, self.nq), u)
 
     def step(self, n_steps: int, exchange_fn) -> None:
-        for _ in range(int(n_steps)):
-            exchange_fn(*self.views())
-            self.hl.hl_step(self.h, 1)
+        import torch
+        with torch.cuda.stream(self.stream):
+            for _ in range(int(n_steps)):
+                exchange_fn(*self.views())
+                self.hl.hl_step(self.h, 1)
 
     def owned_fields(self):
         """Host copies of the owned planes: p (L * plane_nodes, nq), u (dim, L * plane_nodes, nq)."""
@@ -218,10 +220,16 @@ class SlabSolver:
 
 
 def step_slabs(slabs, n_steps: int) -> None:
-    """Step slabs that one process holds on one device (their ghosts exchanged by copies)."""
-    for _ in range(int(n_steps)):
-        views = [s.views() for s in slabs]
-        exchange_local([v[0] for v in views])
-        exchange_local([v[1] for v in views])
-        for s in slabs:
-            s.hl.hl_step(s.h, 1)
+    """Step slabs that one process holds on one device (their ghosts exchanged by copies).
+    All slabs must share one stream, so that copies and steps stay in order."""
+    import torch
+    raw = [getattr(s.stream, "cuda_stream", s.stream) for s in slabs]
+    if any(r != raw[0] for r in raw):
+        raise ValueError("slabs stepped together must share one stream")
+    with torch.cuda.stream(slabs[0].stream):
+        for _ in range(int(n_steps)):
+            views = [s.views() for s in slabs]
+            exchange_local([v[0] for v in views])
+            exchange_local([v[1] for v in views])
+            for s in slabs:
+                s.hl.hl_step(s.h, 1)
