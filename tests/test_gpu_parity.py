@@ -112,7 +112,7 @@ def test_random_state_parity(d, m, ncell, path):
     assert rel_err(ug, uo) <= tol
 
 
-def test_config1_full_1d_standing_mode():
+def test_1d_standing_mode_64_nodes_1000_steps():
     """1D, 64 nodes, m = 3, p = sin(2 pi 3 x), 1000 steps at C_CFL = 0.9: full-run parity,
     and the GPU error against the exact solution is at the oracle's level."""
     d, m, ncell = 1, 3, [64]
@@ -126,7 +126,7 @@ def test_config1_full_1d_standing_mode():
 
 
 @pytest.mark.parametrize("path", [0, 2])
-def test_config2_reduced_full_run(path):
+def test_2d_gaussian_pulse_48x40_200_steps(path):
     """2D m = 3 Gaussian pulse (width 0.05) on 48 x 40 (ragged against every tile shape)
     for the workload's 200 steps."""
     d, m, ncell = 2, 3, [48, 40]
@@ -137,7 +137,7 @@ def test_config2_reduced_full_run(path):
     assert rel_err(pg, po) <= TOL and rel_err(ug, uo) <= TOL
 
 
-def test_config3_reduced_full_run():
+def test_3d_plane_wave_12_cubed_40_steps():
     """3D m = 2 plane wave on 12^3 (ragged against the 128-thread blocks), 40 steps."""
     d, m, ncell = 3, 2, [12, 12, 12]
     dt = I.cfl_dt(ncell)
@@ -175,7 +175,7 @@ def _sampled_step_parity(d, m, ncell, dt, st, warm_steps, n_sample, seed, tile="
 
 
 @pytest.mark.parametrize("tile", ["auto", 0, 9, 12])
-def test_config2_full_size_sampled(tile):
+def test_2d_512_squared_full_size_sampled(tile):
     """512^2, m = 3: the workload the benchmark times, in its autotuned launch configuration
     and on the one-node, paired and p-half-paired tile shapes."""
     d, m, ncell = 2, 3, [512, 512]
@@ -183,7 +183,7 @@ def test_config2_full_size_sampled(tile):
     _sampled_step_parity(d, m, ncell, dt, I.gaussian_pulse(d, m, ncell, dt, seed=1), 20, 4000, 5, tile)
 
 
-def test_config3_full_size_sampled():
+def test_3d_256_cubed_full_size_sampled():
     """256^3, m = 2 plane wave: 14.5 GB of FP64 state, sampled one-step parity."""
     d, m, ncell = 3, 2, [256, 256, 256]
     dt = I.cfl_dt(ncell)
