@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Hermite-leapfrog benchmark on GB300.
 
-Workload (one bench "step"): 2D acoustics on the periodic unit square, 512 x 512
-nodes per grid, m = 3 (16 scaled derivatives per node and field component), FP64,
-seeded Gaussian pressure pulse of width 0.05, 200 leapfrog steps at C_CFL = 0.9.
-Metric: DOF-updates/s = (dim+1) (m+1)^dim N^dim * leapfrog steps / time.
+Headline workload (the default; one bench "step" = one run of it): 3D acoustics on the
+periodic unit cube, 256^3 nodes per grid, m = 2 (27 scaled derivatives per node and field
+component), plane wave p = cos(k.x - |k| t + phi) with seeded wave vector k = 2 pi n,
+|n| <= 8, 100 leapfrog steps at C_CFL = 0.9.
+Metric: DOF-updates/s = (dim+1) (m+1)^dim N^dim * leapfrog steps / time, for the FP64 path
+(`value`), and for each mixed-precision mode beside its L2 error against the exact plane
+wave and the time of the coarsest plain FP64 grid that is at least as accurate.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hl|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hl|reference] [--workload ...]
 
 --impl hl (default): the CUDA library through its C ABI.  `value` is device time
-(CUDA events on the library's stream) with the state resident in HBM, L2 flushed
-between timed steps; `e2e` is the same work timed on the host through
-hl_set_initial / hl_step / hl_get_fields with pinned host buffers.
---impl reference: the CPU oracle (plain C, FP64, OpenMP over nodes) on the host
-cores, each step a bounded sample (one leapfrog step of the same 512^2 problem).
-Under torchrun every rank solves its own independently seeded problem (no
-collective on the data path); rank 0 prints one JSON line.
+(CUDA events on the library's stream) with the state resident in HBM (14.5 GB, larger
+than L2); `e2e` is the same run timed on the host through hl_set_initial / hl_step /
+hl_get_fields with pinned host buffers.
+--impl reference: the CPU oracle (plain C, FP64, OpenMP over nodes) on the host cores,
+each step a bounded sample (one leapfrog step of the same problem on a 32^3 grid).
+Under torchrun every rank solves its own independently seeded problem (no collective on
+the data path); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -36,7 +39,9 @@ if ROOT not in sys.path:
 
 METRIC = "Hermite-leapfrog DOF-updates/s vs FP64 plain at equal L2 error; % roofline"
 UNIT = "DOF-updates/s"
-DIM, M, N, LF_STEPS = 2, 3, 512, 200
+DIM, M, N, LF_STEPS = 3, 2, 256, 100
+WAVE_SEED = 3
+SAMPLE_N = 32            # CPU samples: one leapfrog step of the same problem on 32^3
 L2_FLUSH_BYTES = 256 << 20
 
 # FP64 peak of one GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA per SM
@@ -48,33 +53,40 @@ FP64_PEAK_FLOPS = N_SM * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9
 
 # DRAM traffic of the dominant kernel per launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
-# source is unchanged (keyed by the hash of the kernel header).
-# Captured on this workload (512^2, paired 32x8 tile), mean of two launches,
-# ncu's default cache flush before each launch.
+# source is unchanged (keyed by the hash of the kernel header); per workload.
 TRAFFIC_SOURCE_HASH = "5629d2e800a9a677"
-TRAFFIC_BYTES = {"p_half": 103940096, "u_half": None}
+TRAFFIC_BYTES = {"2d": {"p_half": 103940096, "u_half": None}, "3d": {"p_half": None, "u_half": None}}
 
-WORKLOAD = ("2D acoustics p_t+div u=0, u_t+grad p=0, periodic unit square, 512x512 nodes per grid, "
-            "m=3 (16 scaled derivatives per node per field), FP64, seeded Gaussian pressure pulse "
-            "(width 0.05, random centre), 200 leapfrog steps per bench step at C_CFL=0.9")
+WORKLOAD = ("3D acoustics p_t+div u=0, u_t+grad p=0, periodic unit cube, 256^3 nodes per grid, "
+            "m=2 (27 scaled derivatives per node per field), FP64, plane wave with seeded wave vector "
+            "k=2 pi n, |n|<=8, and phase, 100 leapfrog steps per bench step at C_CFL=0.9")
+WORKLOAD_2D = ("2D acoustics p_t+div u=0, u_t+grad p=0, periodic unit square, 512x512 nodes per grid, "
+               "m=3 (16 scaled derivatives per node per field), FP64, seeded Gaussian pressure pulse "
+               "(width 0.05, random centre), 200 leapfrog steps per bench step at C_CFL=0.9")
+
+
+def headline_config():
+    """The config block both arms print (the reference arm times a bounded CPU sample of it)."""
+    return {"workload": WORKLOAD, "dim": DIM, "m": M, "n_cells": [N] * DIM, "leapfrog_steps_per_step": LF_STEPS,
+            "l2": "inputs larger than L2 (14.5 GB of FP64 state)"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hl", "reference"], default="hl")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-seeds", type=int, default=96, help="learned workload: training seeds")
     ap.add_argument("--test-seeds", type=int, default=32, help="learned workload: held-out seeds")
-    ap.add_argument("--workload", choices=["2d", "1d", "3d", "batch", "mixed3d", "mixed2d", "learned"], default="2d",
-                    help="2d: the headline line; the others measure further rows of the solver")
+    ap.add_argument("--workload", choices=["3d", "2d", "1d", "batch", "mixed3d", "mixed2d", "learned"], default="3d",
+                    help="3d: the headline line; the others measure further rows of the solver")
     return ap.parse_args()
 
 
-def dofs():
-    return (DIM + 1) * (M + 1) ** DIM * N ** DIM
+def dofs(dim=DIM, m=M, n=N):
+    return (dim + 1) * (m + 1) ** dim * n ** dim
 
 
 def kernel_hash():
@@ -133,12 +145,14 @@ class ClockSampler:
 
 
 def cpu_baseline_sample(target_s: float = 15.0):
-    """The oracle as it stands on the host cores: leapfrog steps of the same problem."""
+    """The oracle as it stands on the host cores: leapfrog steps of the headline problem on
+    a 32^3 grid (the per-node work does not depend on the grid size, so DOF-updates/s carry
+    over), for about target_s seconds; and on one thread, one step of a 16^3 grid."""
     import oracle
     from paper_1808_10481_gb300 import inputs as I
-    ncell = [N] * DIM
+    ncell = [SAMPLE_N] * DIM
     dt = I.cfl_dt(ncell)
-    st = I.gaussian_pulse(DIM, M, ncell, dt, seed=1)
+    st = I.plane_wave(M, ncell, dt, seed=WAVE_SEED)
     t0 = time.perf_counter()
     p, u = oracle.run(DIM, M, ncell, dt, st.p, st.u, 1)
     t1 = time.perf_counter() - t0
@@ -150,23 +164,21 @@ def cpu_baseline_sample(target_s: float = 15.0):
     steps = 1 + extra
     secs = t1 + t2
     cores = oracle.threads()
-    # the same oracle on one thread, on a 128^2 grid (one 512^2 step takes half a minute there)
-    n1 = [128] * DIM
+    n1 = [16] * DIM
     dt1 = I.cfl_dt(n1)
-    st1 = I.gaussian_pulse(DIM, M, n1, dt1, seed=1)
+    st1 = I.plane_wave(M, n1, dt1, seed=WAVE_SEED)
     oracle.set_threads(1)
     try:
         t0 = time.perf_counter()
-        oracle.run(DIM, M, n1, dt1, st1.p, st1.u, 2)
+        oracle.run(DIM, M, n1, dt1, st1.p, st1.u, 1)
         s1 = time.perf_counter() - t0
     finally:
         oracle.set_threads(cores)
-    dof1 = (DIM + 1) * (M + 1) ** DIM * 128 ** DIM * 2
-    return {"value": dofs() * steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} leapfrog step(s) of the 512^2 m=3 problem in {secs:.1f} s "
-                      f"(plain C oracle, OpenMP over nodes)",
-            "single_core": {"value": dof1 / s1, "unit": UNIT, "cores": 1,
-                            "sample": f"2 leapfrog steps of the 128^2 m=3 problem in {s1:.1f} s on one thread"}}
+    return {"value": dofs(n=SAMPLE_N) * steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} leapfrog step(s) of the plane-wave problem on a {SAMPLE_N}^3 grid (m=2) in "
+                      f"{secs:.1f} s (plain C oracle, OpenMP over nodes); per-node work as at 256^3",
+            "single_core": {"value": dofs(n=16) / s1, "unit": UNIT, "cores": 1,
+                            "sample": f"1 leapfrog step of the 16^3 m=2 problem in {s1:.1f} s on one thread"}}
 
 
 def run_reference(args, rank):
@@ -174,9 +186,9 @@ def run_reference(args, rank):
         return
     import oracle
     from paper_1808_10481_gb300 import inputs as I
-    ncell = [N] * DIM
+    ncell = [SAMPLE_N] * DIM
     dt = I.cfl_dt(ncell)
-    st = I.gaussian_pulse(DIM, M, ncell, dt, seed=1)
+    st = I.plane_wave(M, ncell, dt, seed=WAVE_SEED)
     p, u = st.p, st.u
     for _ in range(args.warmup):
         p, u = oracle.run(DIM, M, ncell, dt, p, u, 1)
@@ -184,15 +196,19 @@ def run_reference(args, rank):
     for _ in range(args.steps):
         p, u = oracle.run(DIM, M, ncell, dt, p, u, 1)
     secs = time.perf_counter() - t0
-    value = dofs() * args.steps / secs
+    # each step is a bounded sample of one run: one leapfrog step on 32^3 stands for the
+    # 100 leapfrog steps on 256^3 at the same DOF-updates/s
+    value = dofs(n=SAMPLE_N) * args.steps / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "each step = 1 leapfrog step of the 512^2 problem",
-                   "parallelism": "host cores (OpenMP)"},
+        "config": headline_config(),
+        "sample": f"each step = 1 leapfrog step of the same plane-wave problem on a {SAMPLE_N}^3 grid",
+        "parallelism": "host cores (OpenMP)",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                         "sample": f"{args.steps} timed leapfrog steps of the 512^2 m=3 problem"},
+                         "sample": f"{args.steps} timed leapfrog steps of the m=2 plane-wave problem on "
+                                   f"{SAMPLE_N}^3"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -220,17 +236,11 @@ def run_aux(args, rank=0, world=1, dist=None):
     hl.load()
     stream = torch.cuda.current_stream()
     out = {"metric": METRIC, "unit": UNIT, "dtype": "f64", "data": "synthetic", "higher_is_better": True}
-    if args.workload in ("1d", "3d"):
-        if args.workload == "1d":
-            d, m, ncell, lf = 1, 3, [64], 1000
-            dt = I.cfl_dt(ncell)
-            st = I.standing_mode(d, m, ncell, dt, wave=[3])
-            desc = "1D, 64 nodes, m=3, p=sin(2 pi 3 x), u at dt/2 from the exact standing mode, 1000 steps"
-        else:
-            d, m, ncell, lf = 3, 2, [256, 256, 256], 100
-            dt = I.cfl_dt(ncell)
-            st = I.plane_wave(m, ncell, dt, seed=3)
-            desc = "3D, 256^3 nodes per grid, m=2, plane wave |n|<=8 (seed 3), 100 steps"
+    if args.workload == "1d":
+        d, m, ncell, lf = 1, 3, [64], 1000
+        dt = I.cfl_dt(ncell)
+        st = I.standing_mode(d, m, ncell, dt, wave=[3])
+        desc = "1D, 64 nodes, m=3, p=sin(2 pi 3 x), u at dt/2 from the exact standing mode, 1000 steps"
         h = hl.hl_create(d, m, ncell, dt)
         hl.hl_set_stream(h, stream)
         hl.hl_set_initial(h, st.p, st.u)
@@ -270,7 +280,7 @@ def run_aux(args, rank=0, world=1, dist=None):
         modes = {}
         ref_p = None
         mode_list = [("fp64", hl.HL_FP64), ("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)]
-        if d == 2:
+        if d in getattr(hl, "TC_SPLIT_DIMS", (2,)):
             mode_list.append(("tc_split", hl.HL_TC_SPLIT))
         for name, mode in mode_list:
             h = hl.hl_create(d, m, ncell, dt)
@@ -544,27 +554,12 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
     }
 
 
-def main():
-    args = parse()
+def run_headline_2d(args):
+    """The 2D workload line (512^2, m = 3, Gaussian pulse, 200 leapfrog steps per bench step)."""
+    DIM, M, N, LF_STEPS = 2, 3, 512, 200
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-    if args.workload != "2d":
-        import torch
-        torch.cuda.set_device(local_rank)
-        dist = None
-        if world > 1:
-            import torch.distributed as dist
-            dist.init_process_group("nccl")
-        if args.workload == "batch" or rank == 0:
-            run_aux(args, rank, world, dist)
-        if dist:
-            dist.destroy_process_group()
-        return
-
     import numpy as np
     import torch
 
@@ -627,7 +622,7 @@ def main():
         t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max_ms = float(t.item())
-    value = world * dofs() * LF_STEPS * args.steps / (t_max_ms / 1e3)
+    value = world * dofs(DIM, M, N) * LF_STEPS * args.steps / (t_max_ms / 1e3)
 
     # roofline of the dominant kernel (FP64 pipe): algorithmic flops per launch / mean launch time
     fma, add = hl.hl_op_counts(DIM, M)
@@ -639,7 +634,7 @@ def main():
     dom = max(("p_half", "u_half"), key=lambda k: ktimes[k])
     mean_s = ktimes[dom] / kcount[dom] / 1e3
     achieved = flops[dom] / mean_s
-    traffic = TRAFFIC_BYTES.get(dom) if TRAFFIC_SOURCE_HASH == kernel_hash() else None
+    traffic = TRAFFIC_BYTES["2d"].get(dom) if TRAFFIC_SOURCE_HASH == kernel_hash() else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic, "kernel": dom,
                 "kernel_mean_us": mean_s * 1e6,
@@ -670,10 +665,230 @@ def main():
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * dofs() * LF_STEPS * e2e_n / e2e_s, "unit": UNIT,
+    e2e = {"value": world * dofs(DIM, M, N) * LF_STEPS * e2e_n / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": hp.numel() * 8 + hu.numel() * 8,
            "d2h_bytes_per_step": op.numel() * 8 + ou.numel() * 8}
     hl.hl_destroy(h)
+
+    cpu = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "workload": "2d", "config": {"workload": WORKLOAD_2D, "dim": DIM, "m": M, "n_cells": ncell,
+                       "leapfrog_steps_per_step": LF_STEPS, "l2": "flushed between timed steps (256 MiB write)",
+                       "tile": hl.TILES[tile],
+                       "parallelism": f"replicas x{world}: one independently seeded problem per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+            "gpu_launches": int(kcount["p_half"] + kcount["u_half"] + kcount["small"]),
+            "kernel_ms": ktimes,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+
+
+def mode_list(hl, dim):
+    """The mixed-precision modes the library offers for this dim (name, mode)."""
+    out = [("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)]
+    if dim in getattr(hl, "TC_SPLIT_DIMS", (2,)):
+        out.append(("tc_split", hl.HL_TC_SPLIT))
+    return out
+
+
+def run_headline(args):
+    """The headline line: the 3D plane-wave workload, FP64 value and roofline, end to end
+    through host buffers, every mixed-precision mode at its L2 error beside the plain FP64
+    grid of equal error, and the oracle on the host cores."""
+    import numpy as np
+    import torch
+
+    from paper_1808_10481_gb300 import build as libbuild
+    from paper_1808_10481_gb300 import hl
+    from paper_1808_10481_gb300 import inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps are required")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    hl.load()
+
+    ncell = [N] * DIM
+    nnode = N ** DIM
+    nq = (M + 1) ** DIM
+    dt = I.cfl_dt(ncell)
+    seed = WAVE_SEED + rank
+    st = I.plane_wave(M, ncell, dt, seed=seed)
+    t_end = LF_STEPS * dt
+    exact_end = I.plane_wave(0, ncell, dt, seed=seed, t0=t_end).p  # value slot of p at the final time
+    stream = torch.cuda.current_stream()
+    h = hl.hl_create(DIM, M, ncell, dt)
+    hl.hl_set_stream(h, stream)
+    hl.hl_set_initial(h, st.p, st.u)
+    tile, _ = hl.hl_autotune(h, 1)          # tile shape for this GPU and workload (untimed)
+
+    for _ in range(args.warmup):
+        hl.hl_step(h, LF_STEPS)
+    hl.hl_sync(h)
+    hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
+    hl.hl_kernel_times(h)  # reset
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler()
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        hl.hl_step(h, LF_STEPS)          # the 14.5 GB state does not fit the 129 MB L2
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock = clocks.stop()
+    status = hl.hl_sync(h)
+    if status != hl.HL_OK:
+        raise SystemExit(f"solver reported status {status}")
+    dev_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    ktimes, kcount = hl.hl_kernel_times(h)
+    hl.hl_set_option(h, hl.HL_OPT_TIMING, 0)
+    t_max_ms = dev_ms
+    if dist:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max_ms = float(t.item())
+    value = world * dofs() * LF_STEPS * args.steps / (t_max_ms / 1e3)
+
+    # roofline of the dominant kernel (FP64 pipe): algorithmic flops per launch / mean launch time
+    fma, add = hl.hl_op_counts(DIM, M)
+    nz = fma / 2.0
+    bfly = DIM * (1 << DIM) * nq
+    flops = {"p_half": nnode * (2 * nz + DIM * bfly + nq), "u_half": nnode * (2 * nz + bfly + DIM * nq)}
+    dom = max(("p_half", "u_half"), key=lambda k_: ktimes[k_])
+    mean_s = ktimes[dom] / kcount[dom] / 1e3
+    achieved = flops[dom] / mean_s
+    traffic = TRAFFIC_BYTES["3d"].get(dom) if TRAFFIC_SOURCE_HASH == kernel_hash() else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic, "kernel": dom,
+                "kernel_mean_us": mean_s * 1e6,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.070 GHz (unit counts and max clock)",
+                "kernel_share": ktimes[dom] / max(dev_ms, 1e-9)}
+
+    # end to end through the C ABI with pinned host buffers: one run from the initial data
+    hp = torch.empty((nnode, nq), dtype=torch.float64, pin_memory=True)
+    hu = torch.empty((DIM, nnode, nq), dtype=torch.float64, pin_memory=True)
+    hp.copy_(torch.from_numpy(st.p))
+    hu.copy_(torch.from_numpy(st.u))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    hl.hl_set_initial(h, hp, hu)
+    hl.hl_step(h, LF_STEPS)
+    hl.hl_get_fields(h, hp, hu)          # the result overwrites the input buffers
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * dofs() * LF_STEPS / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": hp.numel() * 8 + hu.numel() * 8,
+           "d2h_bytes_per_step": hp.numel() * 8 + hu.numel() * 8,
+           "step": "hl_set_initial + hl_step(100) + hl_get_fields from/to pinned host memory"}
+    fp64_l2 = I.l2_error(DIM, ncell, hp.numpy(), exact_end)
+    hl.hl_destroy(h)
+    del hu
+
+    modes = {}
+    if rank == 0:
+        fp64_run_ms = t_max_ms / args.steps
+        modes["fp64"] = {"value": dofs() * LF_STEPS / (fp64_run_ms / 1e3), "ms_per_run": fp64_run_ms,
+                         "l2_err_p_vs_exact": fp64_l2}
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        for name, mode in mode_list(hl, DIM):
+            hm = hl.hl_create(DIM, M, ncell, dt)
+            try:
+                hl.hl_set_stream(hm, stream)
+                hl.hl_set_precision(hm, mode)
+                hl.hl_set_initial(hm, st.p, st.u)
+                mtile, _ = hl.hl_autotune(hm, 1)
+                hl.hl_set_initial(hm, st.p, st.u)
+                hl.hl_set_option(hm, hl.HL_OPT_TIMING, 1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hl.hl_step(hm, LF_STEPS)
+                e1.record(stream)
+                rc = hl.hl_sync(hm)
+                ms = e0.elapsed_time(e1)
+                kt, kc = hl.hl_kernel_times(hm)
+                hl.hl_get_fields(hm, hp, None)
+            finally:
+                hl.hl_destroy(hm)
+            bytes_run = (3 * DIM + 3) * nq * 8 * nnode * LF_STEPS   # read + write every FP64 DOF once per step
+            gbs = bytes_run / (ms / 1e3) / 1e9
+            modes[name] = {"value": dofs() * LF_STEPS / (ms / 1e3), "ms_per_run": ms, "tile": hl.TILES[mtile],
+                           "p_half_us": 1e3 * kt["p_half"] / max(kc["p_half"], 1),
+                           "u_half_us": 1e3 * kt["u_half"] / max(kc["u_half"], 1),
+                           "l2_err_p_vs_exact": I.l2_error(DIM, ncell, hp.numpy(), exact_end), "status": rc,
+                           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                        "frac": gbs / hbm, "peak_source": "measured" if peaks else "fallback",
+                                        "bytes": "FP64 state read and written once per leapfrog step"}}
+        # equal L2 error: plain FP64 on coarser grids to the same final time; each mode is
+        # set against the fastest FP64 grid whose error is no larger (equal within 1%)
+        ladder = []
+        for n2 in (48, 64, 80, 96, 112, 128, 160):
+            c2 = [n2] * DIM
+            steps2 = int(math.ceil(t_end / I.cfl_dt(c2) - 1e-9))
+            dt2 = t_end / steps2
+            st2 = I.plane_wave(M, c2, dt2, seed=seed)
+            ex2 = I.plane_wave(0, c2, dt2, seed=seed, t0=t_end).p
+            h2 = hl.hl_create(DIM, M, c2, dt2)
+            try:
+                hl.hl_set_stream(h2, stream)
+                hl.hl_set_initial(h2, st2.p, st2.u)
+                hl.hl_step(h2, 2)
+                hl.hl_set_initial(h2, st2.p, st2.u)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hl.hl_step(h2, steps2)
+                e1.record(stream)
+                hl.hl_sync(h2)
+                pg2, _, _, _ = hl.hl_get_fields(h2)
+            finally:
+                hl.hl_destroy(h2)
+            ladder.append({"n": n2, "steps": steps2, "ms_run": e0.elapsed_time(e1),
+                           "l2_err_p_vs_exact": I.l2_error(DIM, c2, pg2, ex2)})
+        ladder.append({"n": N, "steps": LF_STEPS, "ms_run": fp64_run_ms, "l2_err_p_vs_exact": fp64_l2})
+        for name in [k_ for k_ in modes if k_ != "fp64"]:
+            e = modes[name]["l2_err_p_vs_exact"]
+            ok = [r_ for r_ in ladder if r_["l2_err_p_vs_exact"] <= e * 1.01]
+            if ok:
+                r_ = min(ok, key=lambda x: x["ms_run"])
+                modes[name]["fp64_at_equal_error"] = {
+                    "n": r_["n"], "ms_run": r_["ms_run"], "l2_err_p_vs_exact": r_["l2_err_p_vs_exact"],
+                    "speedup_vs_fp64_at_equal_error": r_["ms_run"] / modes[name]["ms_per_run"]}
+            else:
+                modes[name]["fp64_at_equal_error"] = None
+        modes["fp64_error_ladder"] = ladder
+    del hp
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -684,15 +899,41 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dim": DIM, "m": M, "n_cells": ncell,
-                       "leapfrog_steps_per_step": LF_STEPS, "l2": "flushed between timed steps (256 MiB write)",
-                       "tile": hl.TILES[tile],
-                       "parallelism": f"replicas x{world}: one independently seeded problem per GPU"},
+            "config": headline_config(),
+            "workload": "3d", "tile": hl.TILES[tile],
+            "parallelism": f"replicas x{world}: one independently seeded problem per GPU",
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
             "gpu_launches": int(kcount["p_half"] + kcount["u_half"] + kcount["small"]),
-            "kernel_ms": ktimes,
+            "kernel_ms": ktimes, "fp64_l2_err_p_vs_exact": fp64_l2,
+            "modes_vs_fp64_at_equal_l2_error": modes,
         }
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.workload == "3d":
+        run_headline(args)
+        return
+    if args.workload == "2d":
+        run_headline_2d(args)
+        return
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.workload == "batch" or rank == 0:
+        run_aux(args, rank, world, dist)
     if dist:
         dist.destroy_process_group()
 

@@ -352,13 +352,17 @@ int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
  * the kernel parameter bank, the operator table) lives in one file-scope
  * static device array of HL_NOALLOC_SCRATCH_BYTES, held by every GPU that
  * loads the library until the process exits.  Operators larger than that
- * (3D m = 3) are rejected with HL_EINVAL.  The first call on a device looks up
- * the array's device address; make that first call before any stream capture.
+ * (3D m = 3) are rejected with HL_EINVAL.  The first call on a device does a
+ * host-side set-up step: it looks up the array's device address on that device
+ * (cudaGetSymbolAddress, with the device current); that first call should come
+ * before any stream capture.  Every call ends by copying the status word back
+ * to a host variable and synchronising the stream.
  * Every call shares the array and clears the status word it uses: calls that
  * overlap on the GPU (other streams, other host threads) race on it.
- * Synchronises the stream and returns HL_OK, HL_ENONFINITE, HL_EINVAL or
- * HL_ECUDA; hl_last_error(NULL) describes a failure.  Host memory is used
- * only to build the operator table.
+ * p_dev and u_dev must be device memory of the current device (checked with
+ * cudaPointerGetAttributes, which allocates nothing; HL_EINVAL otherwise).
+ * Returns HL_OK, HL_ENONFINITE, HL_EINVAL or HL_ECUDA; hl_last_error(NULL)
+ * describes a failure.  Host memory is used only to build the operator table.
  */
 #define HL_NOALLOC_SCRATCH_BYTES 65536
 int hl_step_noalloc(int dim, int m, const int64_t *n_cells, double dt, double *p_dev, double *u_dev,

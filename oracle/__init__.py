@@ -70,7 +70,7 @@ def _load(prec: str = "f64"):
     if prec in _libs:
         return _libs[prec]
     if prec not in _LIBS:
-        raise ValueError("prec must be 'f64' or 'ld'")
+        raise ValueError("prec must be 'f64' or 'dd'")
     build()
     lib = ctypes.CDLL(_LIBS[prec])
     R = ctypes.c_double if prec == "f64" else DD

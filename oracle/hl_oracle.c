@@ -316,7 +316,11 @@ void oracle_run(int d, int m, const int64_t *ncell, const orc_real *lam, const o
  * with g~_a the exact scaled derivatives prod_k h_k^{a_k}/a_k! d^{a_k} g_k. */
 static orc_real orc_ricker(orc_real t, orc_real f0)
 {
+#ifdef ORC_DD
+    const orc_real pi = orc_dd::make(3.141592653589793116, 1.224646799147353207e-16);  /* pi to 106 bits */
+#else
     const orc_real pi = 3.14159265358979323846;
+#endif
     const orc_real t0 = 1.2 / f0;
     const orc_real arg = pi * pi * f0 * f0 * (t - t0) * (t - t0);
     return (1.0 - 2.0 * arg) * ORC_EXP(-arg);

@@ -96,3 +96,18 @@ def features(p, u, ncell, nodes, feat_scale, t_feature, m=3):
                     col += nq
         out[r, col] = t_feature
     return out
+
+
+def adam_step(params, grads, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba 2015, Algorithm 1), in float64, in place on params,
+    m1 and m2 (dicts of arrays keyed like params); t is the 1-based step count.
+
+    First and second raw moments are exponential averages of g and g*g; each is divided
+    by its bias (1 - beta^t) before the step lr * m1_hat / (sqrt(m2_hat) + eps)."""
+    for k in params:
+        g = grads[k]
+        m1[k] = beta1 * m1[k] + (1.0 - beta1) * g
+        m2[k] = beta2 * m2[k] + (1.0 - beta2) * g * g
+        m1_hat = m1[k] / (1.0 - beta1 ** t)
+        m2_hat = m2[k] / (1.0 - beta2 ** t)
+        params[k] = params[k] - lr * m1_hat / (np.sqrt(m2_hat) + eps)

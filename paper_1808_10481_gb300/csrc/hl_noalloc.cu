@@ -98,8 +98,24 @@ extern "C" int hl_step_noalloc(int dim, int m, const int64_t *n_cells, double dt
 
     std::vector<double> coef;  // host memory only
     if (!hl::build_operator(dim, m, lam, coef)) return fail(HL_EINVAL, "operator construction failed");
+    // both buffers must be device memory of the current device: the kernels
+    // run there and use that device's copy of the scratch array (a pointer into
+    // another GPU would be dereferenced as a peer address)
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return fail(HL_ECUDA, cudaGetErrorString(e));
+    for (const void *ptr : {(const void *)p_dev, (const void *)u_dev}) {
+        cudaPointerAttributes at;
+        e = cudaPointerGetAttributes(&at, ptr);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HL_EINVAL, "p_dev/u_dev are not CUDA device pointers");
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != cur)
+            return fail(HL_EINVAL, "p_dev and u_dev must be device memory of the current device");
+    }
     unsigned char *scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return fail(HL_ECUDA, cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)cuda_stream;
 

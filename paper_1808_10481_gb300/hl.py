@@ -168,6 +168,8 @@ def _dev_ptr(t, count: int):
 # ----------------------------------------------------------------------------- entry points
 def hl_create(dim: int, m: int, n_cells, dt: float) -> Handle:
     lib = load()
+    if 1 <= dim <= 3 and len(n_cells) != dim:   # other dims are the C library's to reject
+        raise ValueError("n_cells must hold dim entries")
     nc = (_I64 * len(n_cells))(*[int(x) for x in n_cells])
     out = _P()
     rc = lib.hl_create(int(dim), int(m), nc, float(dt), ctypes.byref(out))
@@ -333,7 +335,15 @@ def hl_tc_tables(m: int, lam):
 
 def hl_step_noalloc(dim: int, m: int, n_cells, dt: float, p_dev, u_dev, n_steps: int, stream=None) -> int:
     """FP64 steps on caller-owned device buffers (device layout) with no device allocation.
-    Returns HL_OK or HL_ENONFINITE; raises on other failures."""
+    Returns HL_OK or HL_ENONFINITE; raises on other failures.  Both buffers must live on
+    the current CUDA device (the library checks this too)."""
+    if 1 <= dim <= 3 and len(n_cells) != dim:   # other dims are the C library's to reject
+        raise ValueError("n_cells must hold dim entries")
+    for t in (p_dev, u_dev):
+        if getattr(t, "is_cuda", False):
+            import torch
+            if t.device.index != torch.cuda.current_device():
+                raise ValueError("p_dev and u_dev must be on the current CUDA device")
     nnode = int(np.prod(n_cells))
     nq = (m + 1) ** dim
     nc = (_I64 * len(n_cells))(*[int(x) for x in n_cells])

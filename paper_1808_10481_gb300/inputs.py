@@ -173,9 +173,12 @@ def plane_wave(m: int, ncell, dt: float, seed: int, kmax: float = 8.0, t0: float
     hs = np.array([1.0 / c for c in ncell])
 
     def field(dual: bool, t: float) -> np.ndarray:
-        xs = [node_coords(ncell[j], dual) for j in range(3)]
-        X, Y, Z = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
-        theta = (k[0] * X + k[1] * Y + k[2] * Z - kn * t + phi).transpose(2, 1, 0).reshape(-1)
+        # theta at node (ix, iy, iz), x fastest, built by broadcasting the per-axis terms
+        xs = [k[j] * node_coords(ncell[j], dual) for j in range(3)]
+        theta = (xs[2][:, None, None] + xs[1][None, :, None] + xs[0][None, None, :] - kn * t + phi).reshape(-1)
+        # cos(theta + s pi/2) cycles through cos, -sin, -cos, sin
+        c, sn = np.cos(theta), np.sin(theta)
+        quarter = (c, -sn, -c, sn)
         nq = (m + 1) ** 3
         out = np.empty((theta.size, nq))
         for q in range(nq):
@@ -183,7 +186,7 @@ def plane_wave(m: int, ncell, dt: float, seed: int, kmax: float = 8.0, t0: float
             w = 1.0
             for j in range(3):
                 w *= (hs[j] * k[j]) ** a[j] / _fact(a[j])
-            out[:, q] = w * np.cos(theta + sum(a) * math.pi / 2.0)
+            np.multiply(quarter[sum(a) % 4], w, out=out[:, q])
         return out
 
     p = field(False, t0)

@@ -539,3 +539,85 @@ def test_features_follow_translation():
     f1 = mlp.features(Ps, Us, ncell, moved, 0.5, 0.25)
     np.testing.assert_array_equal(f0, f1)
     assert np.all(f0[:, 272] == 0.25) and np.all(f0[:, 273:] == 0.0)
+
+
+def test_features_stencil_fixed_by_coordinate_codes():
+    """Every feature column carries a value that encodes (field, iy, ix, slot), so each
+    column block is checked against the node and component the stencil names: p at the
+    3x3 primal nodes J + {-1,0,1}^2 (y offset outer), then u and then v at the four dual
+    vertices of J's cell, dual nodes J + {-1,0}^2 (y offset outer), then t, then zeros."""
+    from oracle import mlp
+    m, n0, n1 = 3, 11, 7
+    nq = 16
+
+    def code(field, iy, ix, q):
+        return float(((field * 1000 + iy) * 1000 + ix) * 100 + q)
+
+    P = np.array([[code(0, n // n0, n % n0, q) for q in range(nq)] for n in range(n0 * n1)])
+    U = np.array([[[code(1 + c, n // n0, n % n0, q) for q in range(nq)] for n in range(n0 * n1)]
+                  for c in range(2)])
+    nodes = [0, 5, n0 - 1, n0 * (n1 - 1), n0 * n1 - 1, 3 * n0 + 4]
+    X = mlp.features(P, U, [n0, n1], nodes, 1.0, 0.375)
+    for r, node in enumerate(nodes):
+        jx, jy = node % n0, node // n0
+        blocks = [(0, dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        blocks += [(1 + c, vy, vx) for c in range(2) for vy in (-1, 0) for vx in (-1, 0)]
+        for b, (field, oy, ox) in enumerate(blocks):
+            want = [code(field, (jy + oy) % n1, (jx + ox) % n0, q) for q in range(nq)]
+            np.testing.assert_array_equal(X[r, b * nq:(b + 1) * nq], want)
+        assert X[r, 17 * nq] == 0.375
+        assert np.all(X[r, 17 * nq + 1:] == 0.0)
+        assert X.shape[1] == mlp.N_IN == 288
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias-corrected moments are exactly g and g^2, so each
+    step moves w by -lr * g / (|g| + eps): after t steps w_t = w_0 - t lr g / (|g| + eps)."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    w0 = {"a": rng.standard_normal((4, 3)), "b": rng.standard_normal(5)}
+    g = {"a": rng.standard_normal((4, 3)), "b": rng.standard_normal(5) * 1e-3}
+    w = {k: v.copy() for k, v in w0.items()}
+    m1 = {k: np.zeros_like(v) for k, v in w0.items()}
+    m2 = {k: np.zeros_like(v) for k, v in w0.items()}
+    lr, eps = 0.01, 1e-8
+    for t in range(1, 8):
+        mlp.adam_step(w, g, m1, m2, t, lr, eps=eps)
+        for k in w0:
+            want = w0[k] - t * lr * g[k] / (np.abs(g[k]) + eps)
+            np.testing.assert_allclose(w[k], want, rtol=0, atol=1e-13)
+
+
+def test_adam_two_step_weighted_means():
+    """After gradients g1 then g2 the bias-corrected moments are the weighted means
+    (b1 g1 + g2) / (1 + b1) and (b2 g1^2 + g2^2) / (1 + b2) (the exponential averages
+    divided by their weight sums), which fixes which beta goes with which moment."""
+    from oracle import mlp
+    rng = np.random.default_rng(6)
+    b1, b2, lr, eps = 0.9, 0.999, 0.003, 1e-8
+    w0 = {"a": rng.standard_normal(6)}
+    g1, g2 = {"a": rng.standard_normal(6)}, {"a": rng.standard_normal(6)}
+    w = {"a": w0["a"].copy()}
+    m1, m2 = {"a": np.zeros(6)}, {"a": np.zeros(6)}
+    mlp.adam_step(w, g1, m1, m2, 1, lr, b1, b2, eps)
+    w1 = w0["a"] - lr * g1["a"] / (np.abs(g1["a"]) + eps)
+    np.testing.assert_allclose(w["a"], w1, rtol=0, atol=1e-14)
+    mlp.adam_step(w, g2, m1, m2, 2, lr, b1, b2, eps)
+    mh = (b1 * g1["a"] + g2["a"]) / (1 + b1)
+    vh = (b2 * g1["a"] ** 2 + g2["a"] ** 2) / (1 + b2)
+    np.testing.assert_allclose(w["a"], w1 - lr * mh / (np.sqrt(vh) + eps), rtol=0, atol=1e-14)
+
+
+def test_adam_is_invariant_to_gradient_scale_without_eps():
+    """Adam's step is invariant to a positive rescaling of every gradient when eps = 0."""
+    from oracle import mlp
+    rng = np.random.default_rng(7)
+    gs = [{"a": rng.standard_normal(9)} for _ in range(4)]
+    out = []
+    for scale in (1.0, 37.5):
+        w = {"a": np.ones(9)}
+        m1, m2 = {"a": np.zeros(9)}, {"a": np.zeros(9)}
+        for t, g in enumerate(gs, 1):
+            mlp.adam_step(w, {"a": scale * g["a"]}, m1, m2, t, 0.01, eps=0.0)
+        out.append(w["a"])
+    np.testing.assert_allclose(out[0], out[1], rtol=1e-14, atol=0)
