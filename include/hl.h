@@ -66,9 +66,10 @@ enum {
     HL_EINVAL = -1,      /* invalid argument                                   */
     HL_ENOMEM = -2,      /* device or host allocation failed                   */
     HL_ECUDA = -3,       /* a CUDA call failed (handle poisoned)               */
-    HL_ETIMEOUT = -4,    /* a bounded device wait expired (handle poisoned);
-                            reserved: no kernel here waits on another launch
-                            or on the host, so no call returns it today       */
+    HL_ETIMEOUT = -4,    /* a bounded device wait expired (handle poisoned):
+                            the tensor-core kernels wait on their own MMAs
+                            with an iteration limit; no kernel waits on
+                            another launch or on the host                    */
     HL_ENONFINITE = -5,  /* a NaN or Inf appeared in the updated node data     */
     HL_ESTATE = -6       /* call not valid in the handle's state               */
 };
@@ -85,12 +86,14 @@ enum {
                             float-float arithmetic throughout (error-free
                             TwoSum / TwoProduct), about 48 significant bits  */
     HL_TC_SPLIT = 3      /* dim = 2 only: the contraction as exact BF16
-                            tensor-core products (mma.sync, FP32 accumulate):
-                            data (their hi + lo pairs) and operator scaled by
-                            powers of two and cut into 6 base-256 digits; the
-                            digit pairs of the 7 leading levels are summed,
-                            each level exactly, then in float-float; about
-                            46 bits below the block maximum               */
+                            tensor-core products on the fifth-generation
+                            tensor cores (tcgen05.mma, FP32 accumulators in
+                            tensor memory): the binary64 node data of a
+                            128-node tile's region and the operator scaled
+                            by powers of two and cut into 6 base-256 digits;
+                            the digit pairs of the 7 leading levels are
+                            summed, each level exactly, then in float-float;
+                            about 46 bits below the block maximum        */
 };
 
 /*
@@ -230,6 +233,20 @@ int hl_set_source(hl_solver *h, const double *x0, double sigma, double f0, doubl
 int hl_set_sources(hl_solver *h, const double *x0, const double *sigma, const double *f0, const double *amp);
 
 /*
+ * hl_set_wave_speed -- a spatially varying wave speed (Section 4.2), dim = 1:
+ *     p_t + c^2(x) u_x = 0,   u_t + p_x = 0.
+ * c2_primal and c2_dual hold, for every primal and every dual node, the scaled
+ * Taylor coefficients h^i/i! d^i c^2 (i = 0..2m+1) of c^2 at that node: host
+ * arrays [node][2m+2] (the paper's local expansion of the coefficient, with
+ * the printed h!/i! read as h^i/i!).  Each half-step then runs the
+ * Cauchy-Kowalevsky recurrence with these polynomials kept to degree 2m+1
+ * and sums the odd temporal terms to order 2m+1.  Both NULL restores unit
+ * speed.  Requires one grid, HL_FP64, c^2 > 0 and max c * dt < h at the node
+ * values (HL_EINVAL otherwise); takes effect at the next hl_step.
+ */
+int hl_set_wave_speed(hl_solver *h, const double *c2_primal, const double *c2_dual);
+
+/*
  * hl_autotune -- time every tile shape (HL_OPT_TILE) on scratch copies of the
  * state (the solution is not advanced), steps_per_trial steps each after one
  * warm-up step, and keep the fastest.  best_tile receives its index and
@@ -367,6 +384,47 @@ int hl_info(const hl_solver *h, int64_t *nnode, int64_t *nq, int64_t *steps);
 #define HL_NOALLOC_SCRATCH_BYTES 65536
 int hl_step_noalloc(int dim, int m, const int64_t *n_cells, double dt, double *p_dev, double *u_dev,
                     int64_t n_steps, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Modified Hermite-leapfrog scheme (Section 4.3; eqs. hy1, hy2, lfw1, lfw2 and
+ * the pressure-velocity experiment of Table 4), 1D: p_t + u_x = 0, u_t + p_x = 0
+ * on the periodic unit interval, n_cells nodes per grid, h = 1/n_cells.
+ * Both fields live on both grids: primal nodes j h hold (p, u) at t = n dt,
+ * dual nodes (j + 1/2) h hold (p, u) at t = (n + 1/2) dt.  A step updates the
+ * primal grid from the dual grid's interpolants (the cell around primal node j
+ * has dual nodes j - 1 and j as vertices), then the dual grid from the primal
+ * one (vertices: primal nodes j and j + 1).  Even derivative slots take the
+ * difference of the forward and backward temporal Taylor expansions about the
+ * midpoint (eq. hy1), odd slots their sum (eq. lfw2), with the full series of
+ * the degree-2m+1 interpolant; the paper reports uniform order 2m+2.
+ * Host layout of each of the four arrays: f[node][q], q = 0..m (scaled
+ * derivatives h^q/q! d^q f), node x-fastest.  Device layout is private.
+ * Errors as the hl_* calls; hl_mod_last_error(NULL) describes a failed create.
+ */
+typedef struct hl_mod hl_mod;
+
+/* hl_mod_create -- 0 <= m <= 6, n_cells >= 2, 0 < dt < 1/n_cells; state zero. */
+int hl_mod_create(int m, int64_t n_cells, double dt, hl_mod **out);
+void hl_mod_destroy(hl_mod *h);
+const char *hl_mod_last_error(const hl_mod *h);
+/* hl_mod_set_stream -- as hl_set_stream. */
+int hl_mod_set_stream(hl_mod *h, void *cuda_stream);
+/*
+ * hl_mod_set_initial -- copy host data: pp, up (primal grid, t = 0) and pd, ud
+ * (dual grid, t = dt/2), each n_cells*(m+1) doubles; resets the step counter.
+ * Synchronous with respect to the host buffers.
+ */
+int hl_mod_set_initial(hl_mod *h, const double *pp, const double *up, const double *pd, const double *ud);
+/* hl_mod_step -- n_steps >= 0 full steps, stream-ordered (no synchronisation). */
+int hl_mod_step(hl_mod *h, int64_t n_steps);
+/*
+ * hl_mod_get_fields -- copy the state to host buffers (NULL skips one) and
+ * synchronise; HL_ENONFINITE if an update since the last check produced a
+ * NaN or Inf (the data are still copied).
+ */
+int hl_mod_get_fields(hl_mod *h, double *pp, double *up, double *pd, double *ud);
+/* hl_mod_info -- completed steps and the times of the primal and dual data. */
+int hl_mod_info(const hl_mod *h, int64_t *steps, double *t_primal, double *t_dual);
 
 /* ------------------------------------------------------------------------
  * Learned coarse-grid correction (not in the paper).  A per-node multilayer

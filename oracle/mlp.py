@@ -36,29 +36,41 @@ def init_params(rng, n_in=N_IN, n_h=N_H, n_out=N_OUT):
     }
 
 
-def forward(params, X):
-    """Returns (Y, cache) with the pre-activations needed by backward."""
-    Z1 = X @ params["W1"] + params["b1"]
+def _identity(a):
+    return a
+
+
+def forward(params, X, operand_round=None):
+    """Returns (Y, cache) with the pre-activations needed by backward.
+
+    operand_round (optional) is applied to both operands of every matrix product (not to
+    the bias additions): the precision in which the network's tensor-core products see
+    their inputs (BF16 for the learned correction), the sums themselves exact."""
+    r = operand_round or _identity
+    Z1 = r(X) @ r(params["W1"]) + params["b1"]
     H1 = np.maximum(Z1, 0.0)
-    Z2 = H1 @ params["W2"] + params["b2"]
+    Z2 = r(H1) @ r(params["W2"]) + params["b2"]
     H2 = np.maximum(Z2, 0.0)
-    Y = H2 @ params["W3"] + params["b3"]
+    Y = r(H2) @ r(params["W3"]) + params["b3"]
     return Y, (X, Z1, H1, Z2, H2)
 
 
-def loss_and_grads(params, X, T):
-    """Mean squared error over all rows and outputs and its exact gradients."""
-    Y, (X, Z1, H1, Z2, H2) = forward(params, X)
+def loss_and_grads(params, X, T, operand_round=None):
+    """Mean squared error over all rows and outputs and its gradients by back-propagation
+    (exact when operand_round is None; otherwise every product's operands are rounded as
+    in forward, the back-propagation the tensor cores carry out)."""
+    r = operand_round or _identity
+    Y, (X, Z1, H1, Z2, H2) = forward(params, X, operand_round)
     n = Y.size
     R = Y - T
     loss = float(np.sum(R * R) / n)
     dY = 2.0 * R / n
-    g = {"W3": H2.T @ dY, "b3": dY.sum(axis=0)}
-    dH2 = (dY @ params["W3"].T) * (Z2 > 0)
-    g["W2"] = H1.T @ dH2
+    g = {"W3": r(H2).T @ r(dY), "b3": dY.sum(axis=0)}
+    dH2 = (r(dY) @ r(params["W3"]).T) * (Z2 > 0)
+    g["W2"] = r(H1).T @ r(dH2)
     g["b2"] = dH2.sum(axis=0)
-    dH1 = (dH2 @ params["W2"].T) * (Z1 > 0)
-    g["W1"] = X.T @ dH1
+    dH1 = (r(dH2) @ r(params["W2"]).T) * (Z1 > 0)
+    g["W1"] = r(X).T @ r(dH1)
     g["b1"] = dH1.sum(axis=0)
     return loss, g
 

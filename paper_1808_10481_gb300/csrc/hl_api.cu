@@ -80,6 +80,9 @@ static void release(hl_solver *h)
     if (h->Ul) cudaFree(h->Ul);
     if (h->tc_digits) cudaFree(h->tc_digits);
     if (h->tc_expo) cudaFree(h->tc_expo);
+    if (h->tc_shots) cudaFree(h->tc_shots);
+    if (h->c2_primal) cudaFree(h->c2_primal);
+    if (h->c2_dual) cudaFree(h->c2_dual);
     delete h;
 }
 
@@ -268,6 +271,8 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         return set_err(h, HL_EINVAL, "unknown precision mode");
     if (mode == HL_TC_SPLIT && h->dim != 2)
         return set_err(h, HL_EINVAL, "the tensor-core split mode supports dim = 2");
+    if (mode != HL_FP64 && h->c2_primal)
+        return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
     if (mode != HL_FP64) {
         if (h->m > 3 || (h->dim == 3 && h->m > 2))
             return set_err(h, HL_EINVAL, "mixed precision supports m <= 3 (m <= 2 in 3D)");
@@ -278,26 +283,49 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
                 if (std::fabs(s.lam[k] - h->shots[0].lam[k]) > 1e-12 * std::fabs(h->shots[0].lam[k]))
                     return set_err(h, HL_EINVAL, "mixed precision needs the same dt/h on every shot");
     }
-    if (mode != HL_FP64) {
+    if (mode == HL_FP32 || mode == HL_FP32_COMP) {
         // binary32 shadows of both fields (lo parts only for the compensated mode)
         HL_CK(h, cudaStreamSynchronize(h->stream));
         const size_t n = (size_t)h->p_elems;
         if (!h->Ph) HL_CK(h, cudaMalloc(&h->Ph, n * sizeof(float)));
         if (!h->Uh) HL_CK(h, cudaMalloc(&h->Uh, n * h->dim * sizeof(float)));
-        if (mode == HL_FP32_COMP || mode == HL_TC_SPLIT) {
+        if (mode == HL_FP32_COMP) {
             if (!h->Pl) HL_CK(h, cudaMalloc(&h->Pl, n * sizeof(float)));
             if (!h->Ul) HL_CK(h, cudaMalloc(&h->Ul, n * h->dim * sizeof(float)));
         }
     }
-    if (mode == HL_TC_SPLIT && (!h->tc_digits || !h->tc_expo)) {
-        std::vector<uint16_t> dig;
+    if (mode == HL_TC_SPLIT && (!h->tc_digits || !h->tc_expo || !h->tc_shots)) {
+        // the tcgen05 kernels read the binary64 state directly: operator images,
+        // their column exponents and a tile table of 128-node row tiles
+        std::vector<uint16_t> img;
         std::vector<int> ex;
-        if (!build_tc_tables(h->m, h->coef.data(), dig, ex))
+        if (!build_tc5_images(h->m, h->coef.data(), img, ex))
             return set_err(h, HL_EINVAL, "tensor-core tables need m <= 3");
-        if (!h->tc_digits) HL_CK(h, cudaMalloc(&h->tc_digits, dig.size() * sizeof(uint16_t)));
+        std::vector<ShotDesc> sd(h->shots.size());
+        int64_t tiles = 0;
+        for (size_t s = 0; s < h->shots.size(); ++s) {
+            const Shot &sh = h->shots[s];
+            ShotDesc &d = sd[s];
+            for (int k = 0; k < 3; ++k) d.n[k] = (int)sh.n[k];
+            d.tiles[0] = (int)((sh.n[0] + kTc5TileX - 1) / kTc5TileX);
+            d.tiles[1] = (int)sh.n[1];
+            d.tiles[2] = 1;
+            d.nnode = sh.nnode;
+            d.p_off = sh.p_off;
+            d.u_off = sh.u_off;
+            d.tile_begin = (int)tiles;
+            d.pad = 0;
+            tiles += (int64_t)d.tiles[0] * d.tiles[1];
+            if (tiles >= (int64_t(1) << 31)) return set_err(h, HL_EINVAL, "too many tiles for one launch");
+        }
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        if (!h->tc_digits) HL_CK(h, cudaMalloc(&h->tc_digits, img.size() * sizeof(uint16_t)));
         if (!h->tc_expo) HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
-        HL_CK(h, cudaMemcpy(h->tc_digits, dig.data(), dig.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        if (!h->tc_shots) HL_CK(h, cudaMalloc(&h->tc_shots, sd.size() * sizeof(ShotDesc)));
+        HL_CK(h, cudaMemcpy(h->tc_digits, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
         HL_CK(h, cudaMemcpy(h->tc_expo, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
+        HL_CK(h, cudaMemcpy(h->tc_shots, sd.data(), sd.size() * sizeof(ShotDesc), cudaMemcpyHostToDevice));
+        h->tc_tiles = (int)tiles;
     }
     h->precision = mode;
     return HL_OK;
@@ -406,6 +434,10 @@ static int read_status(hl_solver *h, bool clear)
         int rc = resolve_timing(h);
         if (rc) return rc;
     }
+    if (*h->status_host & 2u) {
+        h->poisoned = true;
+        return set_err(h, HL_ETIMEOUT, "a bounded wait on the tensor cores expired (handle poisoned)");
+    }
     if (*h->status_host & 1u) return set_err(h, HL_ENONFINITE, "non-finite value produced by the update");
     return HL_OK;
 }
@@ -477,11 +509,17 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.p_elems = h->p_elems;
     a.tc_digits = h->tc_digits;
     a.tc_expo = h->tc_expo;
+    a.tc_shots = h->tc_shots;
+    a.tc_tiles = h->tc_tiles;
+    a.c2_primal = h->c2_primal;
+    a.c2_dual = h->c2_dual;
+    a.var_lam = h->shots[0].lam[0];
     return a;
 }
 
 static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 {
+    if (a.c2_primal) return dim == 1 ? launch_var_d1(a) : cudaErrorInvalidValue;
     if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : cudaErrorInvalidValue;
     if (a.precision != HL_FP64) {
         switch (dim) {
@@ -617,6 +655,7 @@ extern "C" int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile
     for (int t = 0; t < kNumTiles; ++t) {
         if (ms_per_tile) ms_per_tile[t] = -1.0;
         if (h->dim == 1 && kTiles[t][1] != 1) continue;  // 1D folds tiles into x
+        if (h->precision == HL_TC_SPLIT && t != 0) continue;  // its kernels use their own 128-node tiles
         rc = build_tiles(h, t);
         if (rc) break;
         HL_CK(h, cudaMemcpyAsync(sp, h->p, pb, cudaMemcpyDeviceToDevice, h->stream));
@@ -712,6 +751,46 @@ extern "C" int hl_set_source(hl_solver *h, const double *x0, double sigma, doubl
     for (size_t s = 0; s < ns; ++s)
         for (int k = 0; k < h->dim; ++k) xs[s * h->dim + k] = x0 ? x0[k] : 0.0;
     return hl_set_sources(h, xs.data(), sg.data(), ff.data(), aa.data());
+}
+
+extern "C" int hl_set_wave_speed(hl_solver *h, const double *c2_primal, const double *c2_dual)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (!c2_primal && !c2_dual) {
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        if (h->c2_primal) cudaFree(h->c2_primal);
+        if (h->c2_dual) cudaFree(h->c2_dual);
+        h->c2_primal = h->c2_dual = nullptr;
+        return HL_OK;
+    }
+    if (!c2_primal || !c2_dual) return set_err(h, HL_EINVAL, "give both tables or neither");
+    if (h->dim != 1 || h->shots.size() != 1) return set_err(h, HL_EINVAL, "a variable wave speed needs dim = 1 and one grid");
+    if (h->precision != HL_FP64) return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
+    const int64_t n = h->shots[0].nnode;
+    const int A = 2 * h->m + 2;
+    double cmax2 = 0.0;
+    std::vector<double> tp((size_t)A * n), td((size_t)A * n);  // device layout [i][node]
+    for (int64_t j = 0; j < n; ++j)
+        for (int i = 0; i < A; ++i) {
+            const double a = c2_primal[(size_t)j * A + i], b = c2_dual[(size_t)j * A + i];
+            if (!std::isfinite(a) || !std::isfinite(b)) return set_err(h, HL_EINVAL, "wave speed tables must be finite");
+            if (i == 0) {
+                if (!(a > 0.0) || !(b > 0.0)) return set_err(h, HL_EINVAL, "c^2 must be positive at every node");
+                cmax2 = std::fmax(cmax2, std::fmax(a, b));
+            }
+            tp[(size_t)i * n + j] = a;
+            td[(size_t)i * n + j] = b;
+        }
+    const double hx = 1.0 / (2.0 * h->shots[0].lam[0] / h->shots[0].dt);  // h = dt / (2 lam)
+    if (!(std::sqrt(cmax2) * h->shots[0].dt < hx))
+        return set_err(h, HL_EINVAL, "dt must satisfy max c * dt < h at the node values of c^2");
+    HL_CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->c2_primal) HL_CK(h, cudaMalloc(&h->c2_primal, tp.size() * sizeof(double)));
+    if (!h->c2_dual) HL_CK(h, cudaMalloc(&h->c2_dual, td.size() * sizeof(double)));
+    HL_CK(h, cudaMemcpy(h->c2_primal, tp.data(), tp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HL_CK(h, cudaMemcpy(h->c2_dual, td.data(), td.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return HL_OK;
 }
 
 extern "C" int hl_bind_device(hl_solver *h, double *p_dev, double *u_dev)

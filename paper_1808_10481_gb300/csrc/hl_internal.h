@@ -78,9 +78,17 @@ struct LaunchFp64 {
     // binary32 shadows of P and U for the mixed modes (lo for HL_FP32_COMP and HL_TC_SPLIT)
     float *Ph, *Pl, *Uh, *Ul;
     int64_t p_elems;          // elements of P over all shots (U has dim times more)
-    // HL_TC_SPLIT digit tables (see build_tc_tables): device, kTcOps operators
+    // HL_TC_SPLIT: operator images of both halves (build_tc5_images), their column
+    // exponents (kTcOps x kTcN), and the mode's own tile table (128-node tiles)
     const uint16_t *tc_digits = nullptr;
     const int *tc_expo = nullptr;
+    const ShotDesc *tc_shots = nullptr;
+    int tc_tiles = 0;
+    // variable wave speed (dim = 1, one grid): device tables [i][node] of the scaled
+    // Taylor coefficients of c^2 at the primal and dual nodes, i = 0..2m+1; dt/(2h)
+    const double *c2_primal = nullptr;
+    const double *c2_dual = nullptr;
+    double var_lam = 0.0;
 };
 
 // Tensor-core split mode (HL_TC_SPLIT, dim = 2, m <= 3).  Each operator is the
@@ -95,6 +103,11 @@ constexpr int kTcN = 16;                      // output columns per operator
 constexpr int kTcKS = 136;                    // row stride (bf16) of a digit row: 128 + 8 padding
 constexpr int kTcOpElems = kTcDigits * kTcN * kTcKS;
 bool build_tc_tables(int m, const double *coef, std::vector<uint16_t> &digits, std::vector<int> &expo);
+// The tcgen05 kernels' shared-memory operator images of both halves (2 x 14336
+// BF16), rearranged from build_tc_tables' digits (see hl_tc5.cuh).
+constexpr int kTc5ImageElems = 2 * 14336;
+bool build_tc5_images(int m, const double *coef, std::vector<uint16_t> &image, std::vector<int> &expo);
+constexpr int kTc5TileX = 128;  // nodes per tile of the tcgen05 kernels
 
 cudaError_t launch_fp64_d1(const LaunchFp64 &a);
 cudaError_t launch_fp64_d2(const LaunchFp64 &a);
@@ -103,6 +116,7 @@ cudaError_t launch_mixed_d1(const LaunchFp64 &a);  // precision 1 or 2, m <= 3
 cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
+cudaError_t launch_var_d1(const LaunchFp64 &a);    // variable wave speed, dim = 1, FP64
 
 // message returned by hl_last_error(NULL) for calls that have no handle
 void set_handleless_error(const char *msg);

@@ -78,8 +78,11 @@ struct hl_solver {
     // point sources
     hl::SourceDesc src;
     float *Ph = nullptr, *Pl = nullptr, *Uh = nullptr, *Ul = nullptr;  // mixed-precision shadows
-    uint16_t *tc_digits = nullptr;  // HL_TC_SPLIT operator digit tables (kTcOps operators)
+    uint16_t *tc_digits = nullptr;  // HL_TC_SPLIT operator images of both halves (build_tc5_images)
     int *tc_expo = nullptr;         // and their column exponents
+    hl::ShotDesc *tc_shots = nullptr;  // HL_TC_SPLIT tile table: 128-node tiles of one grid row
+    int tc_tiles = 0;
+    double *c2_primal = nullptr, *c2_dual = nullptr;  // variable wave speed tables (dim = 1), [i][node]
     int *src_node = nullptr, *src_shot = nullptr;
     double *src_table = nullptr;
 };

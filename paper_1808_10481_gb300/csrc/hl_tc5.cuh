@@ -1,0 +1,344 @@
+// Tensor-core split mode (HL_TC_SPLIT), dim = 2, m <= 3, on the fifth-generation
+// tensor cores: tcgen05.mma with the accumulators in tensor memory (TMEM),
+// operands in shared memory, binary64 node data read and written directly.
+//
+// The half-step increment of a node is a dot product of the partner data at
+// the cell's 4 vertices (K = partner component x vertex x slot) with the vertex
+// form of the fused operator (one column per output slot; Section 2, eqs.
+// interp and final1; Section 5).  Both sides are cut into 6 balanced base-256
+// digits after a power-of-two scaling, so every digit product is an exact
+// integer and the sums of one level of digit pairs stay exact in FP32:
+//
+//   data:     x = v 2^-E, |x| < 1, the block's largest binary exponent E;
+//             X = trunc(x 2^48) (an integer of 48 bits), written as
+//             X = sum_i d_i 256^(5-i), d_0 in [-256, 256], d_i in [-128, 127];
+//   operator: column n scaled by 2^-e_n and cut into 6 digits in [-128, 127]
+//             (host tables, build_tc_tables); a 7th zero digit row lets the
+//             first MMA initialise every level's accumulator.
+//
+// Level L = i + j (i data digit, j operator digit) weighs 2^(E + e_n - 14 - 8L).
+// Per level and output the sum over the K = 128 (p-half) or 64 (u-half) terms
+// of at most 6 digit pairs is below 128 (2^15 + 5 2^14) < 2^24, so the tensor
+// core's FP32 accumulation is exact.  Levels L <= 6 are formed (26 digit
+// pairs); the epilogue sums them in float-float, scales by 2^(E + e_n - 14)
+// and adds the increment to the binary64 value.  Quantisation to 48 bits below
+// the block maximum and the dropped levels bound the error by a few 2^-46 of
+// max|data| times the operator's column sums per half-step.
+//
+// One CTA owns a tile of 128 nodes of one grid row (the MMA's M = 128 rows);
+// its region is the 129 x 2 partner nodes of the tile's cells.  The digits of
+// the region are stored once per partner component; the 4 vertex operands are
+// the same digit planes read from 4 different start rows (vertex (vx, vy) of
+// node q is region row q + vx + 129 vy), so no data is duplicated per vertex.
+// Per component and digit i one MMA per vertex multiplies that A (128 x 16)
+// by the operator digits of all levels at once (N = 16 or 32 output columns
+// per level, times the levels i+j <= 6) into TMEM columns starting at level i.
+//
+// Warp roles: all 8 warps load, convert and cut the region (integer pipe);
+// thread 0 issues the MMAs; all 8 warps run the epilogue (warps w and w + 4
+// share TMEM lanes 32 (w % 4) .. + 31 and split the output slots).  Two CTAs
+// run per SM, so one CTA's cutting overlaps the other's MMAs.
+#pragma once
+
+#include <atomic>
+
+#include "hl_fp64.cuh"
+#include "hl_sm100.cuh"
+#include "hl_split.cuh"
+
+namespace hl {
+
+constexpr int kT5Threads = 256;
+constexpr int kT5TileX = 128;                 // nodes per tile (MMA rows)
+constexpr int kT5RX = kT5TileX + 1;           // region nodes per grid row
+constexpr int kT5Rows = 2 * kT5RX;            // region nodes (two grid rows)
+constexpr int kT5RowsPad = 264;               // rows of a digit plane (multiple of 8)
+constexpr int kT5Digits = 6;
+constexpr int kT5Levels = 7;
+constexpr int kT5Chunk = kT5RowsPad * 16;     // bytes of one 8-slot plane: 264 rows of 16 B
+constexpr int kT5Plane = 2 * kT5Chunk;        // one digit of one component (16 slots)
+constexpr int kT5ABytes = kT5Digits * kT5Plane;
+constexpr int kT5BBytes = 28672;              // operator image of one half-step (either half)
+constexpr int kT5SmemBytes = kT5BBytes + kT5ABytes + 64;
+constexpr uint32_t kT5WaitLimit = 1u << 22;   // polls of an mbarrier before giving up
+constexpr unsigned kStatusTimeout = 2u;       // status bit: a bounded wait expired
+
+// Operator image of one half (host-built, build_tc5_images): blocks kb of
+// [2 chunks][7 NPL rows][8 BF16], kb = component * 4 + vertex (p-half, NPL = 16)
+// or vertex (u-half, NPL = 32, rows n = j * 32 + direction * 16 + slot).
+template <bool PHALF>
+struct T5Op {
+    static constexpr int NPL = PHALF ? 16 : 32;        // output columns per level
+    static constexpr int NROWS = kT5Levels * NPL;      // B rows (digit j = 0..6)
+    static constexpr int KB_BYTES = 2 * NROWS * 16;
+    static constexpr int TCOLS = PHALF ? 128 : 256;    // TMEM allocation
+    static_assert((PHALF ? 8 : 4) * KB_BYTES == kT5BBytes, "operator image size");
+};
+
+// Fixed-point form of one binary64 value at the block exponent, with every byte
+// below the top digit biased by 128 (emax is the largest biased exponent of the
+// region, |v| < 2^(emax - 1022) = 2^E):  X = trunc(v 2^(48 - E)), |X| < 2^48,
+// returned as y = X + 0x8080808080, so that byte k of y (k < 5) is d_(5-k) + 128
+// and y >> 40 (arithmetic) is d_0 in [-256, 256].  Integer operations only.
+__device__ __forceinline__ int64_t t5_fixed(double v, int emax)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const int sh = emax + 5 - e;  // >= 5 whenever e <= emax
+    uint64_t mag = 0;
+    if (e != 0 && e != 0x7FF && sh < 64) {
+        const uint64_t m53 = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+        mag = m53 >> sh;
+    }
+    const int64_t x = (hi >> 31) ? -(int64_t)mag : (int64_t)mag;
+    return x + 0x8080808080ll;
+}
+
+// digit i (most significant first) of a biased fixed-point value, as an exact float
+__device__ __forceinline__ float t5_digit(int64_t y, int i)
+{
+    if (i == 0) return __uint_as_float(0x4B000000u + (uint32_t)((int)(y >> 40) + 256)) - 8388864.0f;
+    const uint32_t u = (uint32_t)((uint64_t)y >> (8 * (5 - i))) & 0xFFu;
+    return __uint_as_float(0x4B000000u | u) - 8388736.0f;  // (2^23 + u) - (2^23 + 128)
+}
+
+// BF16 bits of two small-integer floats (exact: at most 8 significant bits)
+__device__ __forceinline__ uint32_t t5_pack(float a, float b)
+{
+    return (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xFFFF0000u);
+}
+
+// exact f * 2^k as binary64 (f normal or zero; integer operations only)
+__device__ __forceinline__ double t5_scaled_f64(float f, int k)
+{
+    const uint32_t b = __float_as_uint(f);
+    if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
+    const int eh = (int)((b >> 23) & 0xFFu) + 896 + k;
+    if (eh <= 0) return 0.0;
+    const uint32_t m = b & 0x7FFFFFu;
+    if (eh >= 2047) return __hiloint2double((int)((b & 0x80000000u) | 0x7FF00000u), 0);
+    return __hiloint2double((int)((b & 0x80000000u) | ((uint32_t)eh << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// Cut the (up to 16) slot values of one region node into its 6 digit planes:
+// src + q * nnode is slot q of the node (slots >= NQ are zero).
+template <int NQ>
+__device__ __forceinline__ void t5_store_row(unsigned char *As, int row, const double *__restrict__ src,
+                                             int64_t nnode, int emax)
+{
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+        if (ch * 8 >= NQ && ch > 0) {  // a chunk of padding slots: zero digits
+#pragma unroll
+            for (int i = 0; i < kT5Digits; ++i)
+                *reinterpret_cast<uint4 *>(As + i * kT5Plane + ch * kT5Chunk + row * 16) = make_uint4(0u, 0u, 0u, 0u);
+            continue;
+        }
+        int64_t y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = t5_fixed(ch * 8 + k < NQ ? __ldg(src + (int64_t)(ch * 8 + k) * nnode) : 0.0, emax);
+#pragma unroll
+        for (int i = 0; i < kT5Digits; ++i) {
+            const uint4 w = make_uint4(t5_pack(t5_digit(y[0], i), t5_digit(y[1], i)),
+                                       t5_pack(t5_digit(y[2], i), t5_digit(y[3], i)),
+                                       t5_pack(t5_digit(y[4], i), t5_digit(y[5], i)),
+                                       t5_pack(t5_digit(y[6], i), t5_digit(y[7], i)));
+            *reinterpret_cast<uint4 *>(As + i * kT5Plane + ch * kT5Chunk + row * 16) = w;
+        }
+    }
+}
+
+template <int M, bool PHALF>
+__global__ void __launch_bounds__(kT5Threads, 2)
+    k_half_tc5(const double *__restrict__ S, double *__restrict__ X, const ShotDesc *__restrict__ shots, int n_shots,
+               const uint4 *__restrict__ Bimg, const int *__restrict__ expo, unsigned *status)
+{
+    constexpr int NQ = (M + 1) * (M + 1);
+    constexpr int NCIN = PHALF ? 2 : 1;  // partner components
+    using Op = T5Op<PHALF>;
+    extern __shared__ __align__(1024) unsigned char t5_sm[];
+    unsigned char *Bs = t5_sm;
+    unsigned char *As = t5_sm + kT5BBytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(As + kT5ABytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
+    int *red = reinterpret_cast<int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int shot;
+    ShotDesc sd;
+    find_shot(shots, n_shots, shot, sd);
+    const int tt = blockIdx.x - sd.tile_begin;
+    const int x0 = (tt % sd.tiles[0]) * kT5TileX;
+    const int y = tt / sd.tiles[0];
+    const int lo = PHALF ? -1 : 0;
+    const int n0 = sd.n[0], n1 = sd.n[1];
+    const int64_t nnode = sd.nnode;
+    const double *Sb = S + (PHALF ? sd.u_off : sd.p_off);
+    double *Xb = X + (PHALF ? sd.p_off : sd.u_off);
+
+    // set-up: tensor memory, the barrier, the operator image, zero pad rows
+    if (warp == 0) {
+        tmem_alloc(smem_addr(tmem_slot), Op::TCOLS);
+        tc_fence_before();
+    }
+    if (tid == 32) mbar_init(smem_addr(mbar), 1);
+    for (int e = tid; e < kT5BBytes / 16; e += kT5Threads) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(Bimg + e);
+    for (int e = tid; e < kT5Digits * 2 * (kT5RowsPad - kT5Rows); e += kT5Threads) {
+        const int dg = e / (2 * (kT5RowsPad - kT5Rows)), ch = (e / (kT5RowsPad - kT5Rows)) % 2;
+        const int r = kT5Rows + e % (kT5RowsPad - kT5Rows);
+        *reinterpret_cast<uint4 *>(As + dg * kT5Plane + ch * kT5Chunk + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+
+    // region node of region row r (periodic wrap on both axes)
+    auto region_node = [&](int r) -> int64_t {
+        const int ry = r / kT5RX, rx = r % kT5RX;
+        int gx = (x0 + lo + rx) % n0;
+        if (gx < 0) gx += n0;
+        int gy = (y + lo + ry) % n1;
+        if (gy < 0) gy += n1;
+        return gx + (int64_t)n0 * gy;
+    };
+    // this thread's region row (tid) and, for threads 0 and 1, rows 256 and 257:
+    // first pass, the block's largest exponent (values are loaded again to be cut)
+    const bool extra = tid < kT5Rows - kT5Threads;
+    const int64_t nd0 = region_node(tid);
+    const int64_t nd1 = extra ? region_node(kT5Threads + tid) : nd0;
+    int emax = 0;
+    bool bad = false;
+#pragma unroll 4
+    for (int e = 0; e < NCIN * NQ; ++e) {
+        const int ex0 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd0)) >> 20) & 0x7FF;
+        const int ex1 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd1)) >> 20) & 0x7FF;
+        bad |= (ex0 == 0x7FF) | (ex1 == 0x7FF);
+        emax = max(emax, max(ex0 == 0x7FF ? 0 : ex0, ex1 == 0x7FF ? 0 : ex1));
+    }
+    report_nonfinite(bad, status);  // a NaN or Inf partner value poisons the update
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    if (lane == 0) red[warp] = emax;
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+#pragma unroll
+    for (int w = 0; w < kT5Threads / 32; ++w) emax = max(emax, red[w]);
+    const int E = emax - 1022;  // every region value is below 2^E in magnitude
+
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < NCIN; ++c) {
+        if (c > 0) ok &= mbar_wait(smem_addr(mbar), (uint32_t)((c - 1) & 1), kT5WaitLimit);  // A is free again
+        t5_store_row<NQ>(As, tid, Sb + (int64_t)c * NQ * nnode + nd0, nnode, emax);
+        if (extra) t5_store_row<NQ>(As, kT5Threads + tid, Sb + (int64_t)c * NQ * nnode + nd1, nnode, emax);
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll
+            for (int i = 0; i < kT5Digits; ++i) {
+                const int nlev = i == 0 ? kT5Levels : min(kT5Digits, kT5Levels - i);
+                const uint32_t idesc = umma_idesc_bf16(128, Op::NPL * nlev);
+#pragma unroll
+                for (int vtx = 0; vtx < 4; ++vtx) {
+                    const uint32_t arow = (uint32_t)((vtx >> 1) * kT5RX + (vtx & 1));
+                    const uint64_t ad = umma_desc(a0 + (uint32_t)(i * kT5Plane) + arow * 16u, kT5Chunk, 128);
+                    const int kb = PHALF ? c * 4 + vtx : vtx;
+                    const uint64_t bd = umma_desc(b0 + (uint32_t)(kb * Op::KB_BYTES), Op::NROWS * 16, 128);
+                    umma_bf16(tmem + (uint32_t)(Op::NPL * i), ad, bd, idesc, (c | i | vtx) != 0 ? 1u : 0u);
+                }
+            }
+            umma_commit(smem_addr(mbar));
+        }
+    }
+    ok &= mbar_wait(smem_addr(mbar), (uint32_t)((NCIN - 1) & 1), kT5WaitLimit);
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+
+    // epilogue: node q of the tile is TMEM lane q; warps w and w + 4 split the outputs
+    const int q = 32 * (warp & 3) + lane;
+    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const int gx = x0 + q;
+    const bool mine = ok && gx < n0;
+    const int64_t node = (int64_t)gx + (int64_t)n0 * y;
+    bad = false;
+    if (ok) {
+        constexpr int NGRP = PHALF ? 1 : 2;  // 8-slot groups per warp
+#pragma unroll
+        for (int g = 0; g < NGRP; ++g) {
+            const int col0 = PHALF ? 8 * (warp >> 2) : 16 * (warp >> 2) + 8 * g;  // column within a level
+            float acc[kT5Levels][8];
+#pragma unroll
+            for (int L = 0; L < kT5Levels; ++L) tmem_ld8(tl + (uint32_t)(L * Op::NPL + col0), acc[L]);
+            tmem_ld_wait();
+            if (mine) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int s = (col0 + j) % 16;
+                    const int oc = PHALF ? 0 : (col0 + j) / 16;  // output component (u-half direction)
+                    if (s >= NQ) continue;
+                    FF tot{0.f, 0.f};
+#pragma unroll
+                    for (int L = kT5Levels - 1; L >= 0; --L) {
+                        const float val = acc[L][j] * __uint_as_float((uint32_t)(127 - 8 * L) << 23);
+                        const FF s2 = ff_two_sum(tot.hi, val);
+                        tot.hi = s2.hi;
+                        tot.lo = __fadd_rn(tot.lo, s2.lo);
+                    }
+                    const FF nrm = ff_two_sum(tot.hi, tot.lo);
+                    const int k0 = E + __ldg(expo + oc * 16 + s) - 14;
+                    const double inc = t5_scaled_f64(nrm.hi, k0) + t5_scaled_f64(nrm.lo, k0);
+                    double *dst = Xb + (int64_t)(oc * NQ + s) * nnode + node;
+                    const double nv = *dst + inc;
+                    *dst = nv;
+                    bad |= nonfinite(nv);
+                }
+            }
+        }
+    }
+    report_nonfinite(bad, status);
+    if (!ok) {
+        // give the MMAs in flight a second bounded wait before tensor memory is released
+        if (tid == 0) atomicOr(status, kStatusTimeout);
+        mbar_wait(smem_addr(mbar), (uint32_t)((NCIN - 1) & 1), kT5WaitLimit);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, Op::TCOLS);
+}
+
+template <int M>
+static cudaError_t run_tc5(const LaunchFp64 &a)
+{
+    if (!a.tc_digits || !a.tc_expo || !a.tc_shots || a.tc_tiles <= 0) return cudaErrorInvalidValue;
+    static std::atomic<uint64_t> opted_in{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(opted_in.load() & bit)) {
+        if ((e = cudaFuncSetAttribute(k_half_tc5<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kT5SmemBytes)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_half_tc5<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kT5SmemBytes)) != cudaSuccess)
+            return e;
+        opted_in.fetch_or(bit);
+    }
+    constexpr int NQ = (M + 1) * (M + 1);
+    const uint4 *bp = reinterpret_cast<const uint4 *>(a.tc_digits);
+    const uint4 *bu = reinterpret_cast<const uint4 *>(a.tc_digits + kT5BBytes / 2);
+    const dim3 grid((unsigned)a.tc_tiles);
+    for (int64_t st = 0; st < a.nsteps; ++st) {
+        if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
+        k_half_tc5<M, true><<<grid, kT5Threads, kT5SmemBytes, a.stream>>>(a.U, a.P, a.tc_shots, a.n_shots, bp,
+                                                                          a.tc_expo, a.status);
+        if (a.src && a.src->active) {
+            if ((e = launch_source(*a.src, a.shots, a.P, NQ, a.step0 + st, a.stream)) != cudaSuccess) return e;
+        }
+        if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
+        k_half_tc5<M, false><<<grid, kT5Threads, kT5SmemBytes, a.stream>>>(a.P, a.U, a.tc_shots, a.n_shots, bu,
+                                                                           a.tc_expo + 16, a.status);
+    }
+    if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
+    return cudaGetLastError();
+}
+
+}  // namespace hl

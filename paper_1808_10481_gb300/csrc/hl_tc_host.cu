@@ -79,4 +79,40 @@ bool build_tc_tables(int m, const double *coef, std::vector<uint16_t> &digits, s
     return true;
 }
 
+// Shared-memory operator images of the tcgen05 kernels (hl_tc5.cuh), one per
+// half-step, each 14336 BF16: blocks kb of [2 K-chunks][7 NPL rows][8 slots]
+// (the no-swizzle K-major layout of the MMA's B operand: 8 rows of 16 bytes
+// per core matrix, row n of block kb at ((kb * 2 + chunk) * 7 NPL + n) * 8).
+//   p-half: kb = velocity component * 4 + vertex, NPL = 16, row n = j * 16 + s;
+//   u-half: kb = vertex, NPL = 32, row n = j * 32 + direction * 16 + s;
+// digit rows j = 0..5 come from build_tc_tables, row block j = 6 is zero (it lets
+// the first MMA of a tile initialise the accumulators of all seven levels).
+bool build_tc5_images(int m, const double *coef, std::vector<uint16_t> &image, std::vector<int> &expo)
+{
+    std::vector<uint16_t> dig;
+    if (!build_tc_tables(m, coef, dig, expo)) return false;
+    image.assign((size_t)kTc5ImageElems, 0);
+    auto digit = [&](int op, int j, int s, int k) -> uint16_t {
+        return dig[(size_t)op * kTcOpElems + ((size_t)j * kTcN + s) * kTcKS + k];
+    };
+    // p-half
+    for (int kb = 0; kb < 8; ++kb)
+        for (int ch = 0; ch < 2; ++ch)
+            for (int n = 0; n < 7 * 16; ++n)
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int j = n / 16, s = n % 16, l = ch * 8 + kk;
+                    image[(((size_t)kb * 2 + ch) * 112 + n) * 8 + kk] = j < kTcDigits ? digit(0, j, s, kb * 16 + l) : 0;
+                }
+    // u-half
+    uint16_t *u = image.data() + kTc5ImageElems / 2;
+    for (int kb = 0; kb < 4; ++kb)
+        for (int ch = 0; ch < 2; ++ch)
+            for (int n = 0; n < 7 * 32; ++n)
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int j = n / 32, dir = (n / 16) % 2, s = n % 16, l = ch * 8 + kk;
+                    u[(((size_t)kb * 2 + ch) * 224 + n) * 8 + kk] = j < kTcDigits ? digit(1 + dir, j, s, kb * 16 + l) : 0;
+                }
+    return true;
+}
+
 }  // namespace hl

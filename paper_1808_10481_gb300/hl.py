@@ -70,6 +70,7 @@ _SIGNATURES = [
                                        ctypes.POINTER(_D)]),
     ("hl_autotune", ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D)]),
     ("hl_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
+    ("hl_set_wave_speed", ctypes.c_int, [_P, _P, _P]),
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -88,6 +89,14 @@ _SIGNATURES = [
     ("hl_apply_correction", ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _D]),
     ("hl_step_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, _P, _P, _I64, _P]),
     ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("hl_mod_create", ctypes.c_int, [ctypes.c_int, _I64, _D, ctypes.POINTER(_P)]),
+    ("hl_mod_destroy", None, [_P]),
+    ("hl_mod_last_error", ctypes.c_char_p, [_P]),
+    ("hl_mod_set_stream", ctypes.c_int, [_P, _P]),
+    ("hl_mod_set_initial", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("hl_mod_step", ctypes.c_int, [_P, _I64]),
+    ("hl_mod_get_fields", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("hl_mod_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_info", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
 ]
 
@@ -297,6 +306,18 @@ def hl_set_precision(h: Handle, mode: int) -> None:
     _check(h, load().hl_set_precision(h.ptr, int(mode)))
 
 
+def hl_set_wave_speed(h: Handle, c2_primal, c2_dual) -> None:
+    """c2 tables (nnode, 2m+2) of scaled Taylor coefficients of c^2 at the primal and dual
+    nodes (dim = 1); None for both restores unit speed."""
+    if c2_primal is None and c2_dual is None:
+        _check(h, load().hl_set_wave_speed(h.ptr, None, None))
+        return
+    n = h.nnode * (2 * h.m + 2)
+    cp = np.ascontiguousarray(c2_primal, dtype=np.float64)   # kept alive across the call
+    cd = np.ascontiguousarray(c2_dual, dtype=np.float64)
+    _check(h, load().hl_set_wave_speed(h.ptr, _host_ptr(cp, n, False), _host_ptr(cd, n, False)))
+
+
 def hl_set_option(h: Handle, option: int, value: int) -> None:
     _check(h, load().hl_set_option(h.ptr, int(option), int(value)))
 
@@ -476,3 +497,66 @@ def hl_targets(fine: Handle, ratio: int, coarse: Handle, nodes, rows: int, out_s
 def hl_apply_correction(coarse: Handle, m: MLP, feat_scale: float, t_feature: float, out_scale: float) -> None:
     _mcheck(m, load().hl_apply_correction(coarse.ptr, m.ptr, ctypes.c_float(feat_scale), ctypes.c_float(t_feature),
                                           float(out_scale)))
+
+
+# ----------------------------------------------------------------------------- modified scheme (1D)
+@dataclass
+class ModHandle:
+    """Handle of the modified Hermite-leapfrog solver (both fields on both grids, 1D)."""
+    ptr: ctypes.c_void_p
+    m: int
+    n: int
+    dt: float
+
+
+def _modcheck(h, rc: int) -> int:
+    if rc != HL_OK:
+        raise HLError(rc, load().hl_mod_last_error(h.ptr if h is not None else None).decode(errors="replace"))
+    return rc
+
+
+def hl_mod_create(m: int, n_cells: int, dt: float) -> ModHandle:
+    out = _P()
+    rc = load().hl_mod_create(int(m), int(n_cells), float(dt), ctypes.byref(out))
+    if rc != HL_OK:
+        raise HLError(rc, load().hl_mod_last_error(None).decode(errors="replace"))
+    return ModHandle(out, int(m), int(n_cells), float(dt))
+
+
+def hl_mod_destroy(h: ModHandle) -> None:
+    if h is not None and h.ptr:
+        load().hl_mod_destroy(h.ptr)
+        h.ptr = _P()
+
+
+def hl_mod_set_stream(h: ModHandle, stream) -> None:
+    raw = getattr(stream, "cuda_stream", stream)
+    _modcheck(h, load().hl_mod_set_stream(h.ptr, ctypes.c_void_p(int(raw) if raw else 0)))
+
+
+def hl_mod_set_initial(h: ModHandle, pp, up, pd, ud) -> None:
+    n = h.n * (h.m + 1)
+    _modcheck(h, load().hl_mod_set_initial(h.ptr, *[_host_ptr(a, n, False) for a in (pp, up, pd, ud)]))
+
+
+def hl_mod_step(h: ModHandle, n_steps: int) -> None:
+    _modcheck(h, load().hl_mod_step(h.ptr, int(n_steps)))
+
+
+def hl_mod_get_fields(h: ModHandle, raise_nonfinite: bool = True):
+    """Returns (pp, up, pd, ud), each (n, m+1) float64."""
+    outs = [np.empty((h.n, h.m + 1), dtype=np.float64) for _ in range(4)]
+    rc = load().hl_mod_get_fields(h.ptr, *[_host_ptr(a, a.size, True) for a in outs])
+    if rc != HL_OK and (rc != HL_ENONFINITE or raise_nonfinite):
+        raise HLError(rc, load().hl_mod_last_error(h.ptr).decode(errors="replace"))
+    return tuple(outs)
+
+
+def hl_mod_info(h: ModHandle):
+    st, tp, td = _I64(), _D(), _D()
+    _modcheck(h, load().hl_mod_info(h.ptr, ctypes.byref(st), ctypes.byref(tp), ctypes.byref(td)))
+    return st.value, tp.value, td.value
+
+
+def hl_mod_last_error(h: ModHandle | None) -> str:
+    return load().hl_mod_last_error(h.ptr if h is not None else None).decode(errors="replace")

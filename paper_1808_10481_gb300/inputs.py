@@ -216,3 +216,69 @@ def l2_error(d: int, ncell, approx: np.ndarray, exact: np.ndarray) -> float:
     vol = float(np.prod([1.0 / n for n in ncell]))
     diff = approx.reshape(-1, approx.shape[-1])[:, 0] - exact.reshape(-1, exact.shape[-1])[:, 0]
     return math.sqrt(vol * float(np.sum(diff * diff)))
+
+
+# ---------------------------------------------------------------- both fields on both grids (1D)
+def standing_mode_1d_both_grids(m: int, n: int, dt: float, wave: int = 1, t0: float = 0.0):
+    """The 1D standing mode p = sin(2 pi w x) cos(2 pi w t), u = -cos(2 pi w x) sin(2 pi w t)
+    with both fields on both grids, as the modified scheme holds them: primal nodes j/n at
+    t0 and dual nodes (j+1/2)/n at t0 + dt/2.  Returns (pp, up, pd, ud), each (n, m+1)."""
+    h = 1.0 / n
+    kap = TWO_PI * wave
+    out = []
+    for dual, t in ((False, t0), (True, t0 + 0.5 * dt)):
+        x = node_coords(n, dual)
+        p = scaled_trig(x, h, m, kap, 0.0) * math.cos(kap * t)
+        u = -scaled_trig(x, h, m, kap, math.pi / 2.0) * math.sin(kap * t)
+        out += [p, u]
+    return tuple(out)
+
+
+# ---------------------------------------------------------------- variable wave speed (1D)
+def c2_taylor_table(n: int, m: int, dual: bool, amp: float = 0.5, wave: int = 1) -> np.ndarray:
+    """Scaled Taylor coefficients h^i/i! d^i c^2 (i = 0..2m+1) of the squared wave speed
+    c^2(x) = 1 + amp sin(2 pi wave x) at the primal (j/n) or dual ((j+1/2)/n) nodes; the
+    unit-interval form of the paper's c^2 = 1 + sin(x)/2 on [0, 2 pi] (amp 1/2, wave 1)."""
+    x = node_coords(n, dual)
+    tab = amp * scaled_trig(x, 1.0 / n, 2 * m + 1, TWO_PI * wave, 0.0)
+    tab[:, 0] += 1.0
+    return tab
+
+
+def c2_max(amp: float = 0.5) -> float:
+    return math.sqrt(1.0 + abs(amp))
+
+
+def _cauchy(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Row-wise product of two truncated Taylor series (same number of terms)."""
+    A = a.shape[1]
+    out = np.zeros_like(a)
+    for k in range(A):
+        for i in range(k + 1):
+            out[:, k] += a[:, i] * b[:, k - i]
+    return out
+
+
+def variable_speed_wave(m: int, n: int, dt: float, t0: float = 0.0):
+    """The paper's variable-speed experiment (Section 4.2) mapped from [0, 2 pi] to the unit
+    interval: p = u = sin(2 pi (x - t)) solves p_t + c^2 u_x = z, u_t + p_x = 0 with
+    c^2 = 1 + sin(2 pi x)/2 and the forcing z = pi sin(2 pi x) cos(2 pi (x - t)).
+    Returns (p at t0 on the primal nodes, u at t0 + dt/2 on the dual nodes) and the forcing
+    callbacks of the two grids: forcing(k, t) = scaled Taylor coefficients (degree 0..2m+1)
+    of d_t^k z at those nodes."""
+    h = 1.0 / n
+    kap = TWO_PI
+    p = scaled_trig(node_coords(n, False), h, m, kap, -kap * t0)
+    u = scaled_trig(node_coords(n, True), h, m, kap, -kap * (t0 + 0.5 * dt))
+
+    def make(dual):
+        x = node_coords(n, dual)
+        s = math.pi * scaled_trig(x, h, 2 * m + 1, kap, 0.0)
+
+        def forcing(k, t):
+            # d_t^k cos(2 pi (x - t)) = (2 pi)^k cos(2 pi (x - t) - k pi/2) = (2 pi)^k sin(. + pi/2 - k pi/2)
+            c = kap ** k * scaled_trig(x, h, 2 * m + 1, kap, -kap * t + math.pi / 2.0 - k * math.pi / 2.0)
+            return _cauchy(s, c)
+        return forcing
+
+    return p, u, make(False), make(True)

@@ -61,50 +61,71 @@ def _batch(rows, seed):
 
 
 # ---------------------------------------------------------------------------------------
-# Element-wise error bounds of the GPU network against the FP64 oracle.  The kernels round
-# every GEMM operand to BF16 (unit roundoff U_BF16 = 2^-8) and accumulate in FP32 (at most
-# K 2^-23 relative to the sum of magnitudes, truncating worst case).  The reference is the
-# oracle run on the BF16 weights and BF16 inputs the tensor cores see, with every other
-# quantity in FP64, so each bound is the propagation of those roundings.
+# Element-wise comparison of the GPU network with the FP64 oracle.  The kernels round every
+# GEMM operand to BF16 (unit roundoff 2^-8) and accumulate in FP32.  The reference is the
+# oracle run with the same operand rounding (oracle.mlp, operand_round = BF16), so the
+# differences left are the FP32 accumulation (at most (K + 2) 2^-23 times the sum of the
+# magnitudes of the terms, truncating worst case), the roundings that the accumulation
+# error can flip (a value within that error of a BF16 rounding boundary), and ReLU masks it
+# can flip (a pre-activation within that error of zero).  Two checks per element:
+#   * a rigorous bound that propagates all three through the network (every element);
+#   * a tight one: |GPU - reference| <= 2^-12 sum |terms| for all but at most 1% of the
+#     elements (flips are rare), so one wrong output column, row or bias block fails.
 U_BF16 = 2.0 ** -8
+TIGHT = 2.0 ** -12
 
 
 def g32(k):
     return (k + 2) * 2.0 ** -23
 
 
-def rounded_operand(a, ea):
-    """Bound of |bf16(a_gpu) - a| given |a_gpu - a| <= ea."""
-    return U_BF16 * (np.abs(a) + ea) + ea
+def rounded(a, ea, nonneg=False):
+    """The reference's BF16 value of a and the bound of |bf16(a_gpu) - bf16(a)| given
+    |a_gpu - a| <= ea (rounding is monotone: bf16(a_gpu) lies between the roundings of the
+    interval's ends)."""
+    ab = bf16(a)
+    lo = np.maximum(a - ea, 0.0) if nonneg else a - ea
+    return ab, np.maximum(np.abs(bf16(a + ea) - ab), np.abs(bf16(lo) - ab))
 
 
 def product_bound(A, dA, B, dB):
-    """|GPU(A B) - A B| for operands whose GPU values (already BF16) differ from A, B by at
-    most dA, dB element-wise, with FP32 accumulation over the inner dimension."""
+    """|GPU(A B) - A B| for BF16 operands whose GPU values differ from A, B by at most dA, dB,
+    with FP32 accumulation over the inner dimension."""
     aA, aB = np.abs(A), np.abs(B)
     return dA @ aB + aA @ dB + dA @ dB + g32(A.shape[1]) * ((aA + dA) @ (aB + dB))
 
 
-def forward_with_bounds(Pb, Xb):
-    Y, (X, Z1, H1, Z2, H2) = M.forward(Pb, Xb)
-    z = np.zeros_like
-    eZ1 = product_bound(Xb, z(Xb), Pb["W1"], z(Pb["W1"])) + g32(0) * np.abs(Z1)
-    eH1 = eZ1
-    dH1 = rounded_operand(H1, eH1)
-    eZ2 = product_bound(H1, dH1, Pb["W2"], z(Pb["W2"])) + g32(0) * np.abs(Z2)
-    eH2 = eZ2
-    dH2 = rounded_operand(H2, eH2)
-    eY = product_bound(H2, dH2, Pb["W3"], z(Pb["W3"])) + g32(0) * np.abs(Y)
-    return Y, eY, dict(Z1=Z1, H1=H1, Z2=Z2, H2=H2, eZ1=eZ1, eH1=eH1, eZ2=eZ2, eH2=eH2, dH1=dH1, dH2=dH2)
-
-
 def masked(P, eP, Z, eZ):
-    """ReLU-mask of a backward product: where |Z| <= eZ the GPU's mask may differ."""
+    """ReLU mask of a backward product: where |Z| <= eZ the GPU's mask may differ."""
     on = Z > 0
-    unsure = np.abs(Z) <= eZ
-    val = P * on
-    err = np.where(unsure, np.abs(P) + eP, eP * on)
-    return val, err
+    return P * on, np.where(np.abs(Z) <= eZ, np.abs(P) + eP, eP * on)
+
+
+def colsum_bound(D, eD, rows):
+    return eD.sum(axis=0) + g32(rows) * (np.abs(D) + eD).sum(axis=0)
+
+
+def forward_reference(P, X):
+    """The oracle's forward with BF16 operands, its element-wise bounds and the magnitude
+    sums of the output products."""
+    Wb = {k: bf16(P[k]) for k in ("W1", "W2", "W3")}
+    Xb = bf16(X)
+    Y, (_, Z1, H1, Z2, H2) = M.forward(P, X, operand_round=bf16)
+    z = np.zeros_like
+    eZ1 = product_bound(Xb, z(Xb), Wb["W1"], z(Wb["W1"])) + 2.0 ** -23 * np.abs(Z1)
+    H1b, d1 = rounded(H1, eZ1, True)
+    eZ2 = product_bound(H1b, d1, Wb["W2"], z(Wb["W2"])) + 2.0 ** -23 * np.abs(Z2)
+    H2b, d2 = rounded(H2, eZ2, True)
+    eY = product_bound(H2b, d2, Wb["W3"], z(Wb["W3"])) + 2.0 ** -23 * np.abs(Y)
+    mag = np.abs(H2b) @ np.abs(Wb["W3"]) + np.abs(P["b3"])
+    return Y, eY, mag, dict(Wb=Wb, Xb=Xb, Z1=Z1, Z2=Z2, H1b=H1b, H2b=H2b, d1=d1, d2=d2, eZ1=eZ1, eZ2=eZ2)
+
+
+def check_elementwise(name, got, ref, bound, mag):
+    err = np.abs(np.asarray(got, dtype=np.float64) - ref)
+    assert np.all(err <= bound), (name, "rigorous", float((err / bound).max()))
+    frac = float(np.mean(err > TIGHT * mag + 1e-30))
+    assert frac <= 0.01, (name, "tight", frac)
 
 
 def test_forward_matches_oracle_elementwise(net):
@@ -116,13 +137,8 @@ def test_forward_matches_oracle_elementwise(net):
     torch.cuda.synchronize()
     params, _ = hl.hl_mlp_params(net)
     P = unpack(params)
-    Pb = {k: (bf16(v) if k.startswith("W") else v) for k, v in P.items()}
-    Y_ref, eY, _ = forward_with_bounds(Pb, bf16(X))
-    Yg = Yd.cpu().numpy().astype(np.float64)
-    err = np.abs(Yg - Y_ref)
-    assert np.all(err <= eY), float((err / eY).max())
-    # the bound is informative: well below the outputs' own size
-    assert float(np.median(eY / np.abs(Y_ref).clip(1e-3))) < 0.05
+    Y_ref, eY, mag, _ = forward_reference(P, X.astype(np.float64))
+    check_elementwise("Y", Yd.cpu().numpy(), Y_ref, eY, mag)
 
 
 def test_gradients_match_oracle_elementwise(net):
@@ -132,42 +148,34 @@ def test_gradients_match_oracle_elementwise(net):
     loss = hl.hl_mlp_loss_grad(net, Xd, Td, rows)
     params, grads = hl.hl_mlp_params(net, want_grads=True)
     P, G = unpack(params), unpack(grads)
-    Pb = {k: (bf16(v) if k.startswith("W") else v) for k, v in P.items()}
-    Xb, T64 = bf16(X), T.astype(np.float64)
-    Y, eY, c = forward_with_bounds(Pb, Xb)
+    X64, T64 = X.astype(np.float64), T.astype(np.float64)
+    Y, eY, _, c = forward_reference(P, X64)
+    loss_ref, G_ref = M.loss_and_grads(P, X64, T64, operand_round=bf16)
     n = Y.size
     R = Y - T64
-    loss_ref = float(np.sum(R * R) / n)
     assert abs(loss - loss_ref) <= float(np.sum(2 * np.abs(R) * eY + eY * eY) / n) + 1e-12 * loss_ref
+    Wb, z = c["Wb"], np.zeros_like
     dY = 2.0 * R / n
     edY = 2.0 * eY / n + 2 * 2.0 ** -23 * np.abs(dY)
-    ddY = rounded_operand(dY, edY)
-    z = np.zeros_like
-    bounds, refs = {}, {}
-    # layer 3
-    refs["W3"] = c["H2"].T @ dY
-    bounds["W3"] = product_bound(c["H2"].T, c["dH2"].T, dY, ddY)
-    refs["b3"] = dY.sum(axis=0)
-    bounds["b3"] = edY.sum(axis=0) + g32(rows) * (np.abs(dY) + edY).sum(axis=0)
-    P2 = dY @ Pb["W3"].T
-    eP2 = product_bound(dY, ddY, Pb["W3"].T, z(Pb["W3"].T))
-    dH2, edH2 = masked(P2, eP2, c["Z2"], c["eZ2"])
-    # layer 2
-    refs["W2"] = c["H1"].T @ dH2
-    bounds["W2"] = product_bound(c["H1"].T, c["dH1"].T, dH2, rounded_operand(dH2, edH2))
-    refs["b2"] = dH2.sum(axis=0)
-    bounds["b2"] = edH2.sum(axis=0) + g32(rows) * (np.abs(dH2) + edH2).sum(axis=0)
-    P1 = dH2 @ Pb["W2"].T
-    eP1 = product_bound(dH2, rounded_operand(dH2, edH2), Pb["W2"].T, z(Pb["W2"].T))
-    dH1, edH1 = masked(P1, eP1, c["Z1"], c["eZ1"])
-    # layer 1 (the GPU's BF16 copy of X is Xb exactly)
-    refs["W1"] = Xb.T @ dH1
-    bounds["W1"] = product_bound(Xb.T, z(Xb.T), dH1, rounded_operand(dH1, edH1))
-    refs["b1"] = dH1.sum(axis=0)
-    bounds["b1"] = edH1.sum(axis=0) + g32(rows) * (np.abs(dH1) + edH1).sum(axis=0)
-    for k in refs:
-        err = np.abs(G[k] - refs[k])
-        assert np.all(err <= bounds[k]), (k, float((err / bounds[k]).max()))
+    dYb, ddY = rounded(dY, edY)
+    bounds, mags = {}, {}
+    bounds["W3"] = product_bound(c["H2b"].T, c["d2"].T, dYb, ddY)
+    mags["W3"] = np.abs(c["H2b"]).T @ np.abs(dYb)
+    bounds["b3"], mags["b3"] = colsum_bound(dY, edY, rows), np.abs(dY).sum(axis=0)
+    P2 = dYb @ Wb["W3"].T
+    dH2, edH2 = masked(P2, product_bound(dYb, ddY, Wb["W3"].T, z(Wb["W3"].T)), c["Z2"], c["eZ2"])
+    dH2b, ddH2 = rounded(dH2, edH2)
+    bounds["W2"] = product_bound(c["H1b"].T, c["d1"].T, dH2b, ddH2)
+    mags["W2"] = np.abs(c["H1b"]).T @ np.abs(dH2b)
+    bounds["b2"], mags["b2"] = colsum_bound(dH2, edH2, rows), np.abs(dH2).sum(axis=0)
+    P1 = dH2b @ Wb["W2"].T
+    dH1, edH1 = masked(P1, product_bound(dH2b, ddH2, Wb["W2"].T, z(Wb["W2"].T)), c["Z1"], c["eZ1"])
+    dH1b, ddH1 = rounded(dH1, edH1)
+    bounds["W1"] = product_bound(c["Xb"].T, z(c["Xb"].T), dH1b, ddH1)   # the GPU's BF16 X is Xb exactly
+    mags["W1"] = np.abs(c["Xb"]).T @ np.abs(dH1b)
+    bounds["b1"], mags["b1"] = colsum_bound(dH1, edH1, rows), np.abs(dH1).sum(axis=0)
+    for k in G_ref:
+        check_elementwise(k, G[k], G_ref[k], bounds[k], mags[k])
 
 
 def test_adam_step_matches_oracle_elementwise(net):
