@@ -283,11 +283,21 @@ enum {
                                 32x8, 64x4 paired in the p-half only; dim = 1
                                 folds the tile into x and never pairs);
                                 hl_autotune picks one                          */
-    HL_OPT_STEP = 5          /* set the step counter n (>= 0) that places the
+    HL_OPT_STEP = 5,         /* set the step counter n (>= 0) that places the
                                 state in time (p at n dt, u at (n + 1/2) dt) and
                                 clocks the point sources; hl_set_initial resets
                                 it to 0, so a run resumed from a checkpoint
                                 sets it back to the checkpoint's step count    */
+    HL_OPT_SPLIT = 6         /* 1 = run each FP64 half-step as the split pair of
+                                Section 6 (the comparison of Figs. 5-6 and
+                                Table 6): an interpolation kernel stores every
+                                node's (2m+2)^dim interpolant coefficients per
+                                partner component (sum-factorised, one axis at
+                                a time) to a device buffer, an evolution kernel
+                                reads them back and sums the Cauchy-Kowalevsky
+                                series; 0 = the fused kernels (default).  One
+                                grid, m <= 3, HL_FP64, unit speed; allocates
+                                dim (2m+2)^dim doubles per node (HL_ENOMEM)   */
 };
 
 #define HL_NUM_TILES 14
@@ -513,6 +523,29 @@ int hl_targets(const hl_solver *fine, int ratio, const hl_solver *coarse, const 
  * owned by the network handle.
  */
 int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_scale, float t_feature, double out_scale);
+
+/*
+ * hl_set_correction -- apply the learned correction inside the stepping loop:
+ * after every every_k_steps-th step of the handle's step count, hl_step runs
+ * on the handle's stream (no host synchronisation, CUDA-graph capturable)
+ *     y = network(features(J)) at every primal node J     (as hl_apply_correction)
+ *     p~(J) += out_scale * y                               (in FP64)
+ * unless the plain solver judges it unsafe.  Fallback rule: the correction is
+ * skipped (the plain step stands) when
+ *     sum_J,q (out_scale y)^2  >  max_ratio^2 * sum_J,q (p~ - p~_before)^2,
+ * p~_before being p before the last plain step: a correction larger than
+ * max_ratio times that step's own change (or a non-finite one) is not taken.
+ * The paper has no learned correction; this is the run-time use of the
+ * coarse-grid correction trained by the hl_mlp_* calls, on a single 2D m = 3
+ * unit-box grid in HL_FP64.  mlp == NULL removes the correction; the network
+ * handle must outlive its use and must not run other work concurrently (its
+ * workspace is used).  Allocates p-sized scratch once (HL_ENOMEM on failure).
+ */
+int hl_set_correction(hl_solver *h, hl_mlp *mlp, int every_k_steps, float feat_scale, float t_feature,
+                      double out_scale, double max_ratio);
+
+/* hl_correction_stats -- corrections applied and skipped so far (synchronises). */
+int hl_correction_stats(hl_solver *h, int64_t *applied, int64_t *skipped);
 
 #ifdef __cplusplus
 }

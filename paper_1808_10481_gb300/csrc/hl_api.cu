@@ -1,6 +1,7 @@
 // C ABI of the Hermite-leapfrog solver (declared in include/hl.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -83,6 +84,13 @@ static void release(hl_solver *h)
     if (h->tc_shots) cudaFree(h->tc_shots);
     if (h->c2_primal) cudaFree(h->c2_primal);
     if (h->c2_dual) cudaFree(h->c2_dual);
+    if (h->split_coef) cudaFree(h->split_coef);
+    if (h->split_beg) cudaFree(h->split_beg);
+    if (h->split_idx) cudaFree(h->split_idx);
+    if (h->split_w) cudaFree(h->split_w);
+    if (h->corr_snap) cudaFree(h->corr_snap);
+    if (h->corr_sums) cudaFree(h->corr_sums);
+    if (h->corr_counts) cudaFree(h->corr_counts);
     delete h;
 }
 
@@ -273,6 +281,8 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         return set_err(h, HL_EINVAL, "the tensor-core split mode supports dim = 2");
     if (mode != HL_FP64 && h->c2_primal)
         return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
+    if (mode != HL_FP64 && h->split_coef)
+        return set_err(h, HL_EINVAL, "the split two-kernel form runs in HL_FP64 only");
     if (mode != HL_FP64) {
         if (h->m > 3 || (h->dim == 3 && h->m > 2))
             return set_err(h, HL_EINVAL, "mixed precision supports m <= 3 (m <= 2 in 3D)");
@@ -360,6 +370,39 @@ extern "C" int hl_set_option(hl_solver *h, int option, int64_t value)
         if (value < 0) return set_err(h, HL_EINVAL, "step counter must be >= 0");
         h->steps = value;  // read when the next hl_step is issued (source clock, field times)
         return HL_OK;
+    case HL_OPT_SPLIT: {
+        if (value < 0 || value > 1) return set_err(h, HL_EINVAL, "split must be 0 or 1");
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        if (value == 0) {
+            if (h->split_coef) cudaFree(h->split_coef);
+            h->split_coef = nullptr;
+            return HL_OK;
+        }
+        if (h->shots.size() != 1 || h->m > 3 || h->precision != HL_FP64 || h->c2_primal)
+            return set_err(h, HL_EINVAL, "the split form needs one grid, m <= 3, HL_FP64 and unit speed");
+        std::vector<int> beg, idx;
+        std::vector<double> w;
+        if (!build_split_terms(h->dim, h->m, h->shots[0].lam, beg, idx, w))
+            return set_err(h, HL_EINVAL, "split term lists failed");
+        int64_t ad = 1;
+        for (int k = 0; k < h->dim; ++k) ad *= 2 * h->m + 2;
+        const size_t cbytes = (size_t)h->dim * ad * h->shots[0].nnode * sizeof(double);
+        cudaError_t e = cudaSuccess;
+        if (!h->split_coef) e = cudaMalloc(&h->split_coef, cbytes);
+        if (e == cudaSuccess && !h->split_beg) e = cudaMalloc(&h->split_beg, beg.size() * sizeof(int));
+        if (e == cudaSuccess && !h->split_idx) e = cudaMalloc(&h->split_idx, idx.size() * sizeof(int));
+        if (e == cudaSuccess && !h->split_w) e = cudaMalloc(&h->split_w, w.size() * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (h->split_coef) cudaFree(h->split_coef);
+            h->split_coef = nullptr;
+            return set_err(h, HL_ENOMEM, std::string("split buffers: ") + cudaGetErrorString(e));
+        }
+        HL_CK(h, cudaMemcpy(h->split_beg, beg.data(), beg.size() * sizeof(int), cudaMemcpyHostToDevice));
+        HL_CK(h, cudaMemcpy(h->split_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+        HL_CK(h, cudaMemcpy(h->split_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return HL_OK;
+    }
     default:
         return set_err(h, HL_EINVAL, "unknown option");
     }
@@ -514,12 +557,17 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.c2_primal = h->c2_primal;
     a.c2_dual = h->c2_dual;
     a.var_lam = h->shots[0].lam[0];
+    a.split_coef = h->split_coef;
+    a.split_beg = h->split_beg;
+    a.split_idx = h->split_idx;
+    a.split_w = h->split_w;
     return a;
 }
 
 static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 {
     if (a.c2_primal) return dim == 1 ? launch_var_d1(a) : cudaErrorInvalidValue;
+    if (a.split_coef && a.precision == HL_FP64) return launch_split(dim, a);
     if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : cudaErrorInvalidValue;
     if (a.precision != HL_FP64) {
         switch (dim) {
@@ -535,6 +583,41 @@ static cudaError_t dispatch(int dim, const LaunchFp64 &a)
     case 3: return launch_fp64_d3(a);
     }
     return cudaErrorInvalidValue;
+}
+
+// The steps of one hl_step call with the learned correction applied after every
+// corr_every-th step of the handle's step count (hl_set_correction): each block of
+// steps runs as plain launches, p is copied before the block's last step (the
+// fallback rule compares the correction with that step's change), then the
+// correction runs on the same stream.  Without a correction: one dispatch.
+static cudaError_t run_steps(hl_solver *h, const LaunchFp64 &a)
+{
+    if (!h->corr_mlp) return dispatch(h->dim, a);
+    const int64_t k = h->corr_every;
+    const size_t pb = (size_t)h->p_elems * sizeof(double);
+    int64_t done = 0;
+    cudaError_t e = cudaSuccess;
+    while (done < a.nsteps) {
+        const int64_t S = a.step0 + done;                 // steps completed before this block
+        const int64_t to_next = k - (S % k);              // 1..k steps to the next correction
+        const int64_t chunk = std::min<int64_t>(to_next, a.nsteps - done);
+        const bool corr = chunk == to_next;
+        LaunchFp64 b = a;
+        b.step0 = S;
+        b.ev = a.ev ? a.ev + 2 * done : nullptr;
+        b.nsteps = corr ? chunk - 1 : chunk;
+        if (b.nsteps > 0 && (e = dispatch(h->dim, b)) != cudaSuccess) return e;
+        if (corr) {
+            if ((e = cudaMemcpyAsync(h->corr_snap, a.P, pb, cudaMemcpyDeviceToDevice, a.stream)) != cudaSuccess) return e;
+            b.step0 = S + chunk - 1;
+            b.ev = a.ev ? a.ev + 2 * (done + chunk - 1) : nullptr;
+            b.nsteps = 1;
+            if ((e = dispatch(h->dim, b)) != cudaSuccess) return e;
+            if ((e = apply_correction_checked(h, a.stream)) != cudaSuccess) return e;
+        }
+        done += chunk;
+    }
+    return e;
 }
 
 extern "C" int hl_step(hl_solver *h, int64_t n_steps)
@@ -557,7 +640,7 @@ extern "C" int hl_step(hl_solver *h, int64_t n_steps)
         HL_CK(h, cudaEventRecord(h->ev_fork, h->stream));
         HL_CK(h, cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0));
         HL_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t e = dispatch(h->dim, a);
+        const cudaError_t e = run_steps(h, a);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -586,7 +669,7 @@ extern "C" int hl_step(hl_solver *h, int64_t n_steps)
         first = h->ev_used;
         a.ev = h->ev_pool.data() + first;
     }
-    const cudaError_t e = dispatch(h->dim, a);
+    const cudaError_t e = run_steps(h, a);
     if (e != cudaSuccess) return fail_cuda(h, e, "hl_step kernel launch");
     if (h->timing) {
         h->pending.push_back({first, n_steps, used_small});
@@ -767,6 +850,7 @@ extern "C" int hl_set_wave_speed(hl_solver *h, const double *c2_primal, const do
     if (!c2_primal || !c2_dual) return set_err(h, HL_EINVAL, "give both tables or neither");
     if (h->dim != 1 || h->shots.size() != 1) return set_err(h, HL_EINVAL, "a variable wave speed needs dim = 1 and one grid");
     if (h->precision != HL_FP64) return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
+    if (h->split_coef) return set_err(h, HL_EINVAL, "the split two-kernel form has unit speed");
     const int64_t n = h->shots[0].nnode;
     const int A = 2 * h->m + 2;
     double cmax2 = 0.0;

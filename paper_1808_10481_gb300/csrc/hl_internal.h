@@ -89,6 +89,11 @@ struct LaunchFp64 {
     const double *c2_primal = nullptr;
     const double *c2_dual = nullptr;
     double var_lam = 0.0;
+    // split two-kernel ablation (HL_OPT_SPLIT): interpolant buffer [comp][coef][node] and
+    // the evolution's term lists (build_split_terms), device
+    double *split_coef = nullptr;
+    const int *split_beg = nullptr, *split_idx = nullptr;
+    const double *split_w = nullptr;
 };
 
 // Tensor-core split mode (HL_TC_SPLIT, dim = 2, m <= 3).  Each operator is the
@@ -117,6 +122,9 @@ cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
 cudaError_t launch_var_d1(const LaunchFp64 &a);    // variable wave speed, dim = 1, FP64
+cudaError_t launch_split(int dim, const LaunchFp64 &a);  // split two-kernel FP64 ablation, m <= 3
+bool build_split_terms(int D, int m, const double lam[3], std::vector<int> &beg, std::vector<int> &idx,
+                       std::vector<double> &w);
 
 // message returned by hl_last_error(NULL) for calls that have no handle
 void set_handleless_error(const char *msg);

@@ -375,6 +375,51 @@ __global__ void k_correct(double *__restrict__ P, int64_t nnode, const float *__
     P[(int64_t)q * nnode + r] += out_scale * (double)Y[e];
 }
 
+// Sums of squares for the correction's fallback rule: sums[0] += (out_scale Y)^2 over
+// every node and slot, sums[1] += (P - snapshot)^2 (the last plain step's change of p).
+__global__ void k_corr_norms(const float *__restrict__ Y, const double *__restrict__ P,
+                             const double *__restrict__ snap, int64_t nnode, double out_scale, double *sums)
+{
+    __shared__ double red[2][256];
+    double a = 0.0, b = 0.0;
+    const int64_t n = nnode * kOut;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / kOut, q = e % kOut;
+        const double c = out_scale * (double)Y[e];
+        const double d = P[q * nnode + r] - snap[q * nnode + r];
+        a = fma(c, c, a);
+        b = fma(d, d, b);
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + o];
+            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(sums, red[0][0]);
+        atomicAdd(sums + 1, red[1][0]);
+    }
+}
+
+// p~ += out_scale Y at every node when the correction passes the fallback rule
+// sum (correction)^2 <= ratio^2 sum (last plain increment)^2 (a NaN fails it);
+// counts[0] counts applied corrections, counts[1] skipped ones
+__global__ void k_correct_checked(double *__restrict__ P, int64_t nnode, const float *__restrict__ Y, double out_scale,
+                                  const double *__restrict__ sums, double ratio2, unsigned long long *counts)
+{
+    const bool ok = sums[0] <= ratio2 * sums[1];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) atomicAdd(counts + (ok ? 0 : 1), 1ull);
+    if (!ok || e >= nnode * kOut) return;
+    const int64_t r = e / kOut, q = e % kOut;
+    P[q * nnode + r] += out_scale * (double)Y[e];
+}
+
 static unsigned blocks_for(int64_t n, int threads)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -469,14 +514,15 @@ static Work work_ptrs(hl_mlp *h, int64_t rows)
     return w;
 }
 
-static cudaError_t forward_into(hl_mlp *h, const float *X, int rows, const Work &w, float *Y)
+static cudaError_t forward_into(hl_mlp *h, const float *X, int rows, const Work &w, float *Y,
+                                cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = gemm({X, kIn, 1}, {h->w + OFF_W1, kH, 1}, w.H1, kH, rows, kH, kIn, h->w + OFF_B1, 1, h->stream)) != cudaSuccess)
+    if ((e = gemm({X, kIn, 1}, {h->w + OFF_W1, kH, 1}, w.H1, kH, rows, kH, kIn, h->w + OFF_B1, 1, st)) != cudaSuccess)
         return e;
-    if ((e = gemm({w.H1, kH, 1}, {h->w + OFF_W2, kH, 1}, w.H2, kH, rows, kH, kH, h->w + OFF_B2, 1, h->stream)) != cudaSuccess)
+    if ((e = gemm({w.H1, kH, 1}, {h->w + OFF_W2, kH, 1}, w.H2, kH, rows, kH, kH, h->w + OFF_B2, 1, st)) != cudaSuccess)
         return e;
-    return gemm({w.H2, kH, 1}, {h->w + OFF_W3, kOut, 1}, Y, kOut, rows, kOut, kH, h->w + OFF_B3, 0, h->stream);
+    return gemm({w.H2, kH, 1}, {h->w + OFF_W3, kOut, 1}, Y, kOut, rows, kOut, kH, h->w + OFF_B3, 0, st);
 }
 
 extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
@@ -566,7 +612,7 @@ extern "C" int hl_mlp_forward(hl_mlp *h, const float *X_dev, int rows, float *Y_
     if (rows == 0) return HL_OK;
     rc = ensure_rows(h, rows);
     if (rc) return rc;
-    MLP_CK(h, forward_into(h, X_dev, rows, work_ptrs(h, rows), Y_dev));
+    MLP_CK(h, forward_into(h, X_dev, rows, work_ptrs(h, rows), Y_dev, h->stream));
     return HL_OK;
 }
 
@@ -579,7 +625,7 @@ extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_de
     if (rc) return rc;
     const Work w = work_ptrs(h, rows);
     const cudaStream_t st = h->stream;
-    MLP_CK(h, forward_into(h, X_dev, rows, w, w.Y));
+    MLP_CK(h, forward_into(h, X_dev, rows, w, w.Y, h->stream));
     MLP_CK(h, cudaMemsetAsync(h->loss, 0, sizeof(double), st));
     const int64_t ny = (int64_t)rows * kOut;
     k_mse<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, T_dev, w.dY, ny, h->loss);
@@ -729,10 +775,97 @@ extern "C" int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_sc
     k_features<<<(unsigned)((nx + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, coarse->u, (int)s.n[0], (int)s.n[1],
                                                                        s.nnode, nullptr, rows, feat_scale, t_feature, X);
     MLP_CK(mlp, cudaGetLastError());
-    MLP_CK(mlp, forward_into(mlp, X, rows, w, w.Y));
+    MLP_CK(mlp, forward_into(mlp, X, rows, w, w.Y, mlp->stream));
     const int64_t ny = (int64_t)rows * kOut;
     k_correct<<<(unsigned)((ny + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, s.nnode, w.Y, rows, out_scale);
     MLP_CK(mlp, cudaGetLastError());
     if (mlp->stream != coarse->stream) MLP_CK(mlp, cudaStreamSynchronize(mlp->stream));
     return HL_OK;
 }
+
+// ---------------------------------------------------------------------------
+// The learned correction inside the stepping loop (hl_set_correction), with the
+// plain solver as fallback: see include/hl.h.
+extern "C" int hl_set_correction(hl_solver *h, hl_mlp *mlp, int every_k_steps, float feat_scale, float t_feature,
+                                 double out_scale, double max_ratio)
+{
+    if (!h) return mlp_err(nullptr, HL_EINVAL, "null solver handle");
+    if (!mlp) {
+        h->corr_mlp = nullptr;
+        return HL_OK;
+    }
+    int rc = solver_ok(h);
+    if (rc) return rc;
+    rc = mlp_check(mlp);
+    if (rc) return rc;
+    if (every_k_steps < 1) return mlp_err(nullptr, HL_EINVAL, "every_k_steps must be >= 1");
+    if (!(out_scale > 0.0) || !std::isfinite(out_scale) || !std::isfinite(feat_scale) || !std::isfinite(t_feature))
+        return mlp_err(nullptr, HL_EINVAL, "scales must be finite (out_scale > 0)");
+    if (!(max_ratio > 0.0)) return mlp_err(nullptr, HL_EINVAL, "max_ratio must be > 0");
+    if (h->precision != HL_FP64) return mlp_err(nullptr, HL_EINVAL, "the learned correction runs with HL_FP64 stepping");
+    const int rows = (int)h->shots[0].nnode;
+    const int64_t per_row = 2 * kH + 2 * kOut + 2 * kH;
+    rc = ensure_rows(mlp, rows + ((int64_t)rows * kIn + per_row - 1) / per_row);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && !h->corr_snap) e = cudaMalloc(&h->corr_snap, (size_t)h->nq * rows * sizeof(double));
+    if (e == cudaSuccess && !h->corr_sums) e = cudaMalloc(&h->corr_sums, 2 * sizeof(double));
+    if (e == cudaSuccess && !h->corr_counts) {
+        e = cudaMalloc(&h->corr_counts, 2 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(h->corr_counts, 0, 2 * sizeof(unsigned long long));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return mlp_err(nullptr, HL_ENOMEM, std::string("correction set-up: ") + cudaGetErrorString(e));
+    }
+    h->corr_mlp = mlp;
+    h->corr_every = every_k_steps;
+    h->corr_feat_scale = feat_scale;
+    h->corr_t_feature = t_feature;
+    h->corr_out_scale = out_scale;
+    h->corr_ratio = max_ratio;
+    return HL_OK;
+}
+
+extern "C" int hl_correction_stats(hl_solver *h, int64_t *applied, int64_t *skipped)
+{
+    if (!h) return mlp_err(nullptr, HL_EINVAL, "null solver handle");
+    unsigned long long c[2] = {0ull, 0ull};
+    if (h->corr_counts) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(c, h->corr_counts, sizeof c, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return mlp_err(nullptr, HL_ECUDA, cudaGetErrorString(e));
+    }
+    if (applied) *applied = (int64_t)c[0];
+    if (skipped) *skipped = (int64_t)c[1];
+    return HL_OK;
+}
+
+namespace hl {
+
+// Stream-ordered: features of every node, the network, the fallback rule's sums, the
+// checked FP64 addition.  Runs on st (the solver's stream); no host synchronisation.
+cudaError_t apply_correction_checked(hl_solver *h, cudaStream_t st)
+{
+    hl_mlp *mlp = h->corr_mlp;
+    const Shot &s = h->shots[0];
+    const int rows = (int)s.nnode;
+    const Work w = work_ptrs(mlp, rows);
+    float *X = w.dH1 + (int64_t)rows * kH;
+    const int64_t nx = (int64_t)rows * kIn;
+    k_features<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(h->p, h->u, (int)s.n[0], (int)s.n[1], s.nnode, nullptr,
+                                                              rows, h->corr_feat_scale, h->corr_t_feature, X);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = forward_into(mlp, X, rows, w, w.Y, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->corr_sums, 0, 2 * sizeof(double), st)) != cudaSuccess) return e;
+    const int64_t ny = (int64_t)rows * kOut;
+    k_corr_norms<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, h->p, h->corr_snap, s.nnode, h->corr_out_scale,
+                                                      h->corr_sums);
+    k_correct_checked<<<(unsigned)((ny + 255) / 256), 256, 0, st>>>(h->p, s.nnode, w.Y, h->corr_out_scale,
+                                                                    h->corr_sums, h->corr_ratio * h->corr_ratio,
+                                                                    h->corr_counts);
+    return cudaGetLastError();
+}
+
+}  // namespace hl

@@ -33,6 +33,8 @@ struct Shot {
 
 }  // namespace hl
 
+struct hl_mlp;
+
 struct hl_solver {
     int dim = 0, m = 0;
     int64_t nq = 0;
@@ -83,7 +85,24 @@ struct hl_solver {
     hl::ShotDesc *tc_shots = nullptr;  // HL_TC_SPLIT tile table: 128-node tiles of one grid row
     int tc_tiles = 0;
     double *c2_primal = nullptr, *c2_dual = nullptr;  // variable wave speed tables (dim = 1), [i][node]
+    // split two-kernel ablation (HL_OPT_SPLIT)
+    double *split_coef = nullptr;
+    int *split_beg = nullptr, *split_idx = nullptr;
+    double *split_w = nullptr;
+    // learned correction inside hl_step (hl_set_correction)
+    hl_mlp *corr_mlp = nullptr;
+    int corr_every = 0;
+    float corr_feat_scale = 1.f, corr_t_feature = 0.f;
+    double corr_out_scale = 1.0, corr_ratio = 1.0;
+    double *corr_snap = nullptr;               // p before the last plain step of a block
+    double *corr_sums = nullptr;               // fallback rule: sum correction^2, sum increment^2
+    unsigned long long *corr_counts = nullptr; // applied, skipped
     int *src_node = nullptr, *src_shot = nullptr;
     double *src_table = nullptr;
 };
 
+
+namespace hl {
+// the learned correction of hl_set_correction, stream-ordered (hl_mlp.cu)
+cudaError_t apply_correction_checked(hl_solver *h, cudaStream_t st);
+}  // namespace hl

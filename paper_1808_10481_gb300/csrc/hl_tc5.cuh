@@ -148,6 +148,26 @@ __device__ __forceinline__ void t5_store_row(unsigned char *As, int row, const d
     }
 }
 
+// as t5_store_row, from values already in registers
+template <int NQ>
+__device__ __forceinline__ void t5_store_row_regs(unsigned char *As, int row, const double (&v)[NQ], int emax)
+{
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+        int64_t y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) y[k] = t5_fixed(ch * 8 + k < NQ ? v[(ch * 8 + k) % NQ] : 0.0, emax);
+#pragma unroll
+        for (int i = 0; i < kT5Digits; ++i) {
+            const uint4 w = make_uint4(t5_pack(t5_digit(y[0], i), t5_digit(y[1], i)),
+                                       t5_pack(t5_digit(y[2], i), t5_digit(y[3], i)),
+                                       t5_pack(t5_digit(y[4], i), t5_digit(y[5], i)),
+                                       t5_pack(t5_digit(y[6], i), t5_digit(y[7], i)));
+            *reinterpret_cast<uint4 *>(As + i * kT5Plane + ch * kT5Chunk + row * 16) = w;
+        }
+    }
+}
+
 template <int M, bool PHALF>
 __global__ void __launch_bounds__(kT5Threads, 2)
     k_half_tc5(const double *__restrict__ S, double *__restrict__ X, const ShotDesc *__restrict__ shots, int n_shots,
@@ -198,19 +218,36 @@ __global__ void __launch_bounds__(kT5Threads, 2)
         if (gy < 0) gy += n1;
         return gx + (int64_t)n0 * gy;
     };
-    // this thread's region row (tid) and, for threads 0 and 1, rows 256 and 257:
-    // first pass, the block's largest exponent (values are loaded again to be cut)
+    // this thread's region row (tid), all its values loaded at once and kept in registers;
+    // threads 0 and 1 also own rows 256 and 257 (loaded here for the exponent, again to be cut)
     const bool extra = tid < kT5Rows - kT5Threads;
     const int64_t nd0 = region_node(tid);
     const int64_t nd1 = extra ? region_node(kT5Threads + tid) : nd0;
+    // component 0 stays in registers for its cut; the others (p-half) are read for their
+    // exponents now and again when they are cut (from L1/L2)
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = __ldg(Sb + (int64_t)q * nnode + nd0);
     int emax = 0;
     bool bad = false;
-#pragma unroll 4
-    for (int e = 0; e < NCIN * NQ; ++e) {
-        const int ex0 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd0)) >> 20) & 0x7FF;
-        const int ex1 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd1)) >> 20) & 0x7FF;
-        bad |= (ex0 == 0x7FF) | (ex1 == 0x7FF);
-        emax = max(emax, max(ex0 == 0x7FF ? 0 : ex0, ex1 == 0x7FF ? 0 : ex1));
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int ex = (__double2hiint(v[q]) >> 20) & 0x7FF;
+        bad |= ex == 0x7FF;
+        emax = max(emax, ex == 0x7FF ? 0 : ex);
+    }
+#pragma unroll
+    for (int e = NQ; e < NCIN * NQ; ++e) {
+        const int ex = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd0)) >> 20) & 0x7FF;
+        bad |= ex == 0x7FF;
+        emax = max(emax, ex == 0x7FF ? 0 : ex);
+    }
+    if (extra) {
+        for (int e = 0; e < NCIN * NQ; ++e) {
+            const int ex = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd1)) >> 20) & 0x7FF;
+            bad |= ex == 0x7FF;
+            emax = max(emax, ex == 0x7FF ? 0 : ex);
+        }
     }
     report_nonfinite(bad, status);  // a NaN or Inf partner value poisons the update
     emax = __reduce_max_sync(0xFFFFFFFFu, emax);
@@ -226,7 +263,13 @@ __global__ void __launch_bounds__(kT5Threads, 2)
 #pragma unroll
     for (int c = 0; c < NCIN; ++c) {
         if (c > 0) ok &= mbar_wait(smem_addr(mbar), (uint32_t)((c - 1) & 1), kT5WaitLimit);  // A is free again
-        t5_store_row<NQ>(As, tid, Sb + (int64_t)c * NQ * nnode + nd0, nnode, emax);
+        if (c == 0) {
+            t5_store_row_regs<NQ>(As, tid, v, emax);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[q] = __ldg(Sb + (int64_t)(c * NQ + q) * nnode + nd0);
+            t5_store_row_regs<NQ>(As, tid, v, emax);
+        }
         if (extra) t5_store_row<NQ>(As, kT5Threads + tid, Sb + (int64_t)c * NQ * nnode + nd1, nnode, emax);
         fence_async_smem();
         __syncthreads();
@@ -249,19 +292,29 @@ __global__ void __launch_bounds__(kT5Threads, 2)
             umma_commit(smem_addr(mbar));
         }
     }
-    ok &= mbar_wait(smem_addr(mbar), (uint32_t)((NCIN - 1) & 1), kT5WaitLimit);
-    ok = __syncthreads_and(ok);
-    tc_fence_after();
-
-    // epilogue: node q of the tile is TMEM lane q; warps w and w + 4 split the outputs
+    // epilogue: node q of the tile is TMEM lane q; warps w and w + 4 split the outputs.
+    // The node's own values are loaded while the last MMAs run.
+    constexpr int NGRP = PHALF ? 1 : 2;  // 8-slot groups per warp
     const int q = 32 * (warp & 3) + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const int gx = x0 + q;
-    const bool mine = ok && gx < n0;
     const int64_t node = (int64_t)gx + (int64_t)n0 * y;
+    double own[NGRP][8];
+#pragma unroll
+    for (int g = 0; g < NGRP; ++g) {
+        const int col0 = PHALF ? 8 * (warp >> 2) : 16 * (warp >> 2) + 8 * g;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int s = (col0 + j) % 16, oc = PHALF ? 0 : (col0 + j) / 16;
+            own[g][j] = (s < NQ && gx < n0) ? Xb[(int64_t)(oc * NQ + s) * nnode + node] : 0.0;
+        }
+    }
+    ok &= mbar_wait(smem_addr(mbar), (uint32_t)((NCIN - 1) & 1), kT5WaitLimit);
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    const bool mine = ok && gx < n0;
     bad = false;
     if (ok) {
-        constexpr int NGRP = PHALF ? 1 : 2;  // 8-slot groups per warp
 #pragma unroll
         for (int g = 0; g < NGRP; ++g) {
             const int col0 = PHALF ? 8 * (warp >> 2) : 16 * (warp >> 2) + 8 * g;  // column within a level
@@ -286,9 +339,8 @@ __global__ void __launch_bounds__(kT5Threads, 2)
                     const FF nrm = ff_two_sum(tot.hi, tot.lo);
                     const int k0 = E + __ldg(expo + oc * 16 + s) - 14;
                     const double inc = t5_scaled_f64(nrm.hi, k0) + t5_scaled_f64(nrm.lo, k0);
-                    double *dst = Xb + (int64_t)(oc * NQ + s) * nnode + node;
-                    const double nv = *dst + inc;
-                    *dst = nv;
+                    const double nv = own[g][j] + inc;
+                    Xb[(int64_t)(oc * NQ + s) * nnode + node] = nv;
                     bad |= nonfinite(nv);
                 }
             }

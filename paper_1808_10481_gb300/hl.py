@@ -26,6 +26,7 @@ HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
 HL_OPT_STEP = 5
+HL_OPT_SPLIT = 6
 HL_NUM_TILES = 14
 HL_NOALLOC_SCRATCH_BYTES = 65536
 HL_TC_TABLE_ELEMS, HL_TC_EXPO_ELEMS = 39168, 48
@@ -87,6 +88,8 @@ _SIGNATURES = [
     ("hl_features", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
     ("hl_targets", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _D, _P]),
     ("hl_apply_correction", ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_float, _D]),
+    ("hl_set_correction", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _D, _D]),
+    ("hl_correction_stats", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     ("hl_step_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_I64), _D, _P, _P, _I64, _P]),
     ("hl_op_counts", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_mod_create", ctypes.c_int, [ctypes.c_int, _I64, _D, ctypes.POINTER(_P)]),
@@ -492,6 +495,23 @@ def hl_targets(fine: Handle, ratio: int, coarse: Handle, nodes, rows: int, out_s
     rc = load().hl_targets(fine.ptr, int(ratio), coarse.ptr, _iptr(nodes, rows), int(rows), float(out_scale),
                            _fptr(T, rows * HL_MLP_OUT))
     _mcheck(None, rc)
+
+
+def hl_set_correction(h: Handle, m, every_k_steps: int = 1, feat_scale: float = 1.0, t_feature: float = 0.0,
+                      out_scale: float = 1.0, max_ratio: float = 1.0) -> None:
+    """Apply the network's correction inside hl_step after every k-th step (m=None removes it);
+    corrections larger than max_ratio times the last plain step's change are skipped."""
+    rc = load().hl_set_correction(h.ptr, m.ptr if m is not None else None, int(every_k_steps),
+                                  ctypes.c_float(feat_scale), ctypes.c_float(t_feature), float(out_scale),
+                                  float(max_ratio))
+    _mcheck(None, rc)
+
+
+def hl_correction_stats(h: Handle):
+    """Returns (applied, skipped) corrections so far."""
+    a, sk = _I64(), _I64()
+    _mcheck(None, load().hl_correction_stats(h.ptr, ctypes.byref(a), ctypes.byref(sk)))
+    return a.value, sk.value
 
 
 def hl_apply_correction(coarse: Handle, m: MLP, feat_scale: float, t_feature: float, out_scale: float) -> None:

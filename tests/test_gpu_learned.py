@@ -341,3 +341,93 @@ def test_learned_correction_gains_on_held_out_pulses():
         for hc, hf, _ in held:
             hl.hl_destroy(hc)
             hl.hl_destroy(hf)
+
+
+def _pulse_solver(ncell, seed=3):
+    st = I.gaussian_pulse(2, 3, ncell, I.cfl_dt(ncell), seed=seed, width=0.1)
+    h = hl.hl_create(2, 3, ncell, I.cfl_dt(ncell))
+    hl.hl_set_initial(h, st.p, st.u)
+    return h
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_set_correction_equals_the_manual_loop_bitwise(graph):
+    """hl_set_correction(k = 4) over 12 steps of one hl_step call gives, bit for bit, what
+    three rounds of hl_step(4) + hl_apply_correction give; with a permissive fallback bound
+    all three corrections are applied (also inside a captured CUDA graph)."""
+    nc = [32, 24]
+    net = hl.hl_mlp_create(99)
+    try:
+        a = _pulse_solver(nc)
+        b = _pulse_solver(nc)
+        try:
+            hl.hl_set_option(a, hl.HL_OPT_GRAPH, graph)
+            hl.hl_set_correction(a, net, 4, 1.0, 0.0, 1e-4, 1e30)
+            hl.hl_step(a, 12)
+            pa, ua, _, _ = hl.hl_get_fields(a)
+            assert hl.hl_correction_stats(a) == (3, 0)
+            for _ in range(3):
+                hl.hl_step(b, 4)
+                hl.hl_apply_correction(b, net, 1.0, 0.0, 1e-4)
+            pb, ub, _, _ = hl.hl_get_fields(b)
+            np.testing.assert_array_equal(pa, pb)
+            np.testing.assert_array_equal(ua, ub)
+        finally:
+            hl.hl_destroy(a)
+            hl.hl_destroy(b)
+    finally:
+        hl.hl_mlp_destroy(net)
+
+
+@pytest.mark.parametrize("bad", ["huge", "nan"])
+def test_correction_fallback_keeps_the_plain_step(bad):
+    """Weights injected on the host make the correction far larger than a plain step's change
+    (or non-finite): every correction is skipped and the state equals the plain solver's bit
+    for bit; the skips are counted."""
+    nc = [32, 24]
+    net = hl.hl_mlp_create(5)
+    try:
+        params, _ = hl.hl_mlp_params(net)
+        params = params.copy()
+        if bad == "huge":
+            params[-16:] = 1e6          # output bias: every correction is 1e6 * out_scale
+        else:
+            params[-16:] = np.nan
+        hl.hl_mlp_params(net, set_params=params)
+        a = _pulse_solver(nc)
+        b = _pulse_solver(nc)
+        try:
+            hl.hl_set_correction(a, net, 3, 1.0, 0.0, 1.0, 2.0)
+            hl.hl_step(a, 9)
+            hl.hl_step(b, 9)
+            pa, ua, _, _ = hl.hl_get_fields(a)
+            pb, ub, _, _ = hl.hl_get_fields(b)
+            np.testing.assert_array_equal(pa, pb)
+            np.testing.assert_array_equal(ua, ub)
+            assert hl.hl_correction_stats(a) == (0, 3)
+        finally:
+            hl.hl_destroy(a)
+            hl.hl_destroy(b)
+    finally:
+        hl.hl_mlp_destroy(net)
+
+
+def test_set_correction_validation():
+    net = hl.hl_mlp_create(1)
+    h3 = hl.hl_create(2, 2, [16, 16], 0.05)
+    h = _pulse_solver([16, 16])
+    try:
+        with pytest.raises(hl.HLError):
+            hl.hl_set_correction(h3, net, 2, 1.0, 0.0, 1.0, 1.0)   # m = 2: the network is for m = 3
+        with pytest.raises(hl.HLError):
+            hl.hl_set_correction(h, net, 0, 1.0, 0.0, 1.0, 1.0)
+        with pytest.raises(hl.HLError):
+            hl.hl_set_correction(h, net, 2, 1.0, 0.0, -1.0, 1.0)
+        hl.hl_set_correction(h, net, 2, 1.0, 0.0, 1e-6, 1.0)
+        hl.hl_set_correction(h, None)
+        hl.hl_step(h, 4)
+        assert hl.hl_correction_stats(h) == (0, 0)
+    finally:
+        hl.hl_destroy(h)
+        hl.hl_destroy(h3)
+        hl.hl_mlp_destroy(net)
