@@ -246,6 +246,33 @@ int hl_set_sources(hl_solver *h, const double *x0, const double *sigma, const do
  */
 int hl_set_wave_speed(hl_solver *h, const double *c2_primal, const double *c2_dual);
 
+/* Wall kinds for hl_set_walls. */
+enum {
+    HL_WALL_PERIODIC = 0,   /* no wall along the axis                              */
+    HL_WALL_DIRICHLET = 1,  /* p = 0 on the walls (pressure release; a perfect
+                               conductor for E_z in Maxwell TM form): p odd across
+                               the wall, the normal velocity even, tangential odd */
+    HL_WALL_NEUMANN = 2     /* d_n p = 0 (rigid): p even, normal velocity odd      */
+};
+
+/*
+ * hl_set_walls -- reflecting walls by ghost mirroring (Section 5.2, eq.
+ * Boundary and the mirroring that follows it; Section 5.3 runs Maxwell's TM
+ * equations, this system with p = E_z and u = (-H_y, H_x), through the same
+ * walls).  kinds: dim entries (HL_WALL_*), NULL removes the walls.
+ * The handle's grid must be laid out for walls: along a walled axis of N
+ * cells of width h it has N + 2 planes spaced h (hl_create_spacing): plane 0
+ * is an unused primal plane and a dual ghost, planes 1 .. N+1 the primal
+ * nodes 0 .. N (both walls included), planes 1 .. N the dual nodes 0 .. N-1,
+ * plane N+1 the second dual ghost.  Before every p-half hl_step fills, axis
+ * by axis, the dual ghosts with the mirror images of dual planes 1 and N
+ * (slot a times s (-1)^(a_k), s the parity of the velocity component across
+ * the wall) and zeroes primal plane 0, on the handle's stream (no host
+ * synchronisation; captured with the steps in graph mode).  One grid, HL_FP64
+ * or HL_TC_SPLIT, at least 4 planes along walled axes; HL_EINVAL otherwise.
+ */
+int hl_set_walls(hl_solver *h, const int *kinds);
+
 /*
  * hl_autotune -- time every tile shape (HL_OPT_TILE) on scratch copies of the
  * state (the solution is not advanced), steps_per_trial steps each after one

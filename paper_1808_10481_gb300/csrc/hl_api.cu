@@ -283,6 +283,8 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
     if (mode != HL_FP64 && h->split_coef)
         return set_err(h, HL_EINVAL, "the split two-kernel form runs in HL_FP64 only");
+    if ((mode == HL_FP32 || mode == HL_FP32_COMP) && h->walls_active)
+        return set_err(h, HL_EINVAL, "walls run in HL_FP64 or HL_TC_SPLIT");
     if (mode != HL_FP64) {
         if (h->m > 3 || (h->dim == 3 && h->m > 2))
             return set_err(h, HL_EINVAL, "mixed precision supports m <= 3 (m <= 2 in 3D)");
@@ -592,6 +594,20 @@ static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 // correction runs on the same stream.  Without a correction: one dispatch.
 static cudaError_t run_steps(hl_solver *h, const LaunchFp64 &a)
 {
+    if (h->walls_active) {
+        // the ghost planes are filled before every p-half: one step per dispatch
+        cudaError_t e = cudaSuccess;
+        const int n[3] = {(int)h->shots[0].n[0], (int)h->shots[0].n[1], (int)h->shots[0].n[2]};
+        for (int64_t st = 0; st < a.nsteps; ++st) {
+            if ((e = launch_fill_ghosts(a.U, a.P, n, h->dim, h->m, h->walls, a.stream)) != cudaSuccess) return e;
+            LaunchFp64 b = a;
+            b.nsteps = 1;
+            b.step0 = a.step0 + st;
+            b.ev = a.ev ? a.ev + 2 * st : nullptr;
+            if ((e = dispatch(h->dim, b)) != cudaSuccess) return e;
+        }
+        return e;
+    }
     if (!h->corr_mlp) return dispatch(h->dim, a);
     const int64_t k = h->corr_every;
     const size_t pb = (size_t)h->p_elems * sizeof(double);
@@ -874,6 +890,30 @@ extern "C" int hl_set_wave_speed(hl_solver *h, const double *c2_primal, const do
     if (!h->c2_dual) HL_CK(h, cudaMalloc(&h->c2_dual, td.size() * sizeof(double)));
     HL_CK(h, cudaMemcpy(h->c2_primal, tp.data(), tp.size() * sizeof(double), cudaMemcpyHostToDevice));
     HL_CK(h, cudaMemcpy(h->c2_dual, td.data(), td.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return HL_OK;
+}
+
+extern "C" int hl_set_walls(hl_solver *h, const int *kinds)
+{
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (!kinds) {
+        h->walls_active = false;
+        for (int k = 0; k < 3; ++k) h->walls[k] = 0;
+        return HL_OK;
+    }
+    if (h->shots.size() != 1) return set_err(h, HL_EINVAL, "walls need one grid");
+    if (h->precision == HL_FP32 || h->precision == HL_FP32_COMP)
+        return set_err(h, HL_EINVAL, "walls run in HL_FP64 or HL_TC_SPLIT (the FP32 modes keep shadows)");
+    bool any = false;
+    for (int k = 0; k < h->dim; ++k) {
+        if (kinds[k] < HL_WALL_PERIODIC || kinds[k] > HL_WALL_NEUMANN) return set_err(h, HL_EINVAL, "unknown wall kind");
+        if (kinds[k] != HL_WALL_PERIODIC && h->shots[0].n[k] < 4)
+            return set_err(h, HL_EINVAL, "a walled axis needs at least 4 planes (2 cells and 2 ghosts)");
+        any |= kinds[k] != HL_WALL_PERIODIC;
+    }
+    for (int k = 0; k < 3; ++k) h->walls[k] = k < h->dim ? kinds[k] : 0;
+    h->walls_active = any;
     return HL_OK;
 }
 

@@ -123,6 +123,8 @@ cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
 cudaError_t launch_var_d1(const LaunchFp64 &a);    // variable wave speed, dim = 1, FP64
 cudaError_t launch_split(int dim, const LaunchFp64 &a);  // split two-kernel FP64 ablation, m <= 3
+// ghost planes of the walled axes (kinds: 0 periodic, 1 dirichlet, 2 neumann), in axis order
+cudaError_t launch_fill_ghosts(double *U, double *P, const int *n, int dim, int m, const int *kinds, cudaStream_t st);
 bool build_split_terms(int D, int m, const double lam[3], std::vector<int> &beg, std::vector<int> &idx,
                        std::vector<double> &w);
 

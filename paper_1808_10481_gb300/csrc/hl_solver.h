@@ -89,6 +89,9 @@ struct hl_solver {
     double *split_coef = nullptr;
     int *split_beg = nullptr, *split_idx = nullptr;
     double *split_w = nullptr;
+    // reflecting walls (hl_set_walls): kind per axis, 0 = periodic
+    int walls[3] = {0, 0, 0};
+    bool walls_active = false;
     // learned correction inside hl_step (hl_set_correction)
     hl_mlp *corr_mlp = nullptr;
     int corr_every = 0;

@@ -27,6 +27,7 @@ HL_OPT_GRAPH = 3
 HL_OPT_TILE = 4
 HL_OPT_STEP = 5
 HL_OPT_SPLIT = 6
+HL_WALL_PERIODIC, HL_WALL_DIRICHLET, HL_WALL_NEUMANN = 0, 1, 2
 HL_NUM_TILES = 14
 HL_NOALLOC_SCRATCH_BYTES = 65536
 HL_TC_TABLE_ELEMS, HL_TC_EXPO_ELEMS = 39168, 48
@@ -72,6 +73,7 @@ _SIGNATURES = [
     ("hl_autotune", ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D)]),
     ("hl_set_precision", ctypes.c_int, [_P, ctypes.c_int]),
     ("hl_set_wave_speed", ctypes.c_int, [_P, _P, _P]),
+    ("hl_set_walls", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("hl_set_option", ctypes.c_int, [_P, ctypes.c_int, _I64]),
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -319,6 +321,18 @@ def hl_set_wave_speed(h: Handle, c2_primal, c2_dual) -> None:
     cp = np.ascontiguousarray(c2_primal, dtype=np.float64)   # kept alive across the call
     cd = np.ascontiguousarray(c2_dual, dtype=np.float64)
     _check(h, load().hl_set_wave_speed(h.ptr, _host_ptr(cp, n, False), _host_ptr(cd, n, False)))
+
+
+def hl_set_walls(h: Handle, kinds) -> None:
+    """kinds: one HL_WALL_* per axis (or the names 'periodic'/'dirichlet'/'neumann'); None removes them."""
+    if kinds is None:
+        _check(h, load().hl_set_walls(h.ptr, None))
+        return
+    names = {"periodic": HL_WALL_PERIODIC, "dirichlet": HL_WALL_DIRICHLET, "neumann": HL_WALL_NEUMANN}
+    vals = [names[k] if isinstance(k, str) else int(k) for k in kinds]
+    if len(vals) != h.dim:
+        raise ValueError("one wall kind per axis")
+    _check(h, load().hl_set_walls(h.ptr, (ctypes.c_int * h.dim)(*vals)))
 
 
 def hl_set_option(h: Handle, option: int, value: int) -> None:

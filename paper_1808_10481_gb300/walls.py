@@ -186,8 +186,8 @@ class WalledSolver:
 
     ncell: cells per axis; walls: one kind per axis (or one for all); length:
     L_k per axis (default 1).  The state lives in two device buffers bound to
-    the handle (device layout); before every step the u ghost planes are
-    filled on the handle's stream."""
+    the handle (device layout); the library fills the u ghost planes before
+    every step inside hl_step (hl_set_walls), so a run of n steps is one call."""
 
     def __init__(self, dim: int, m: int, ncell, dt: float, walls, length=None, stream=None):
         import torch
@@ -208,8 +208,7 @@ class WalledSolver:
         self.p = torch.zeros(self.nq * nnode, dtype=torch.float64, device="cuda")
         self.u = torch.zeros(dim * self.nq * nnode, dtype=torch.float64, device="cuda")
         hl.hl_bind_device(self.h, self.p, self.u)
-        self.views = field_views(self.p, self.u, dim, m, self.local, "device")
-        self.tables = mirror_tables(dim, m, self.walls, "device", like=self.p)
+        hl.hl_set_walls(self.h, self.walls)
 
     def set_initial(self, p, u) -> None:
         """Walled-domain host-layout data: p at t = 0 on the primal nodes, u at dt/2 on the dual nodes."""
@@ -217,11 +216,7 @@ class WalledSolver:
         self.hl.hl_set_initial(self.h, np.ascontiguousarray(p_loc), np.ascontiguousarray(u_loc))
 
     def step(self, n_steps: int) -> None:
-        import torch
-        with torch.cuda.stream(self.stream):
-            for _ in range(int(n_steps)):
-                fill_ghosts(*self.views, self.dim, self.walls, "device", self.tables)
-                self.hl.hl_step(self.h, 1)
+        self.hl.hl_step(self.h, int(n_steps))
 
     def fields(self):
         """Host copies of the walled domain's p (prod p_counts, nq) and u (dim, prod u_counts, nq)."""

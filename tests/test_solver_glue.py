@@ -56,9 +56,23 @@ def _fake_binding():
         return (np.ascontiguousarray(h.p.view(h.nq, h.nn).numpy().T),
                 np.ascontiguousarray(h.u.view(h.dim, h.nq, h.nn).numpy().transpose(0, 2, 1)))
 
+    def set_walls(h, kinds):
+        h.walls = None if kinds is None else list(kinds)
+    hl.hl_set_walls = set_walls
+
     def step(h, n):
-        p, u = oracle.run(h.dim, h.m, h.n, h.dt, *host(h), int(n), inv_h=h.inv_h)
-        set_initial(h, p, u)
+        # as the library: with walls, the ghost planes are filled (in the device layout)
+        # before every step; without, the steps run at once
+        walls = getattr(h, "walls", None)
+        if walls is None:
+            p, u = oracle.run(h.dim, h.m, h.n, h.dt, *host(h), int(n), inv_h=h.inv_h)
+            set_initial(h, p, u)
+            return
+        tables = W.mirror_tables(h.dim, h.m, walls, "device", like=h.p)
+        for _ in range(int(n)):
+            W.fill_ghosts(*W.field_views(h.p, h.u, h.dim, h.m, h.n, "device"), h.dim, walls, "device", tables)
+            p, u = oracle.run(h.dim, h.m, h.n, h.dt, *host(h), 1, inv_h=h.inv_h)
+            set_initial(h, p, u)
     hl.hl_step = step
     hl.hl_get_fields = lambda h: host(h) + (0.0, 0.0)
     hl.hl_destroy = lambda h: None

@@ -346,3 +346,85 @@ def test_pulse_reflects_with_the_walls_sign(kind, sign):
     assert np.abs(got_p[:, 0] - want).max() < 1e-3
     if kind == "dirichlet":
         assert abs(got_p[0, 0]) < 1e-12 and abs(got_p[N, 0]) < 1e-12
+
+
+def _tm_mode(m, N, L, t_p, t_u, a=16, b=16):
+    """Maxwell TM field E_z = sin(kx x) sin(ky y) cos(w t) on [0, L]^2 with perfectly
+    conducting walls (E_z = 0 on all four), as p = E_z and u = (-H_y, H_x):
+    u_x = -(kx/w) cos(kx x) sin(ky y) sin(w t), u_y = -(ky/w) sin(kx x) cos(ky y) sin(w t),
+    kx = 2 pi a, ky = 2 pi b, w = |k|.  Returns the walled-domain host layout (p on the
+    (N+1)^2 primal nodes at t_p, u on the N^2 dual nodes at t_u)."""
+    h = L / N
+    kx, ky = 2 * math.pi * a, 2 * math.pi * b
+    w = math.hypot(kx, ky)
+    xp = np.arange(N + 1) * h
+    xd = (np.arange(N) + 0.5) * h
+
+    def tensor(fx, fy):  # x fastest, slot a_x fastest
+        return np.einsum("ia,jb->jiba", fx, fy).reshape(fx.shape[0] * fy.shape[0], -1)
+    sx, sy = I.scaled_trig(xp, h, m, kx, 0.0), I.scaled_trig(xp, h, m, ky, 0.0)
+    p = tensor(sx, sy) * math.cos(w * t_p)
+    sxd, syd = I.scaled_trig(xd, h, m, kx, 0.0), I.scaled_trig(xd, h, m, ky, 0.0)
+    cxd, cyd = I.scaled_trig(xd, h, m, kx, math.pi / 2), I.scaled_trig(xd, h, m, ky, math.pi / 2)
+    u = np.stack([-(kx / w) * tensor(cxd, syd), -(ky / w) * tensor(sxd, cyd)]) * math.sin(w * t_u)
+    return p, u
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("m", [3, 4, 5, 6])
+def test_maxwell_tm_with_conducting_walls_converges(m):
+    """Section 5.3's high-frequency Maxwell TM experiment on the GPU through hl_set_walls:
+    omega_x = omega_y = 8 pi on [-1, 1] is 16 periods per unit on the walled square
+    [0, 1/2]^2 here, perfect conductors (HL_WALL_DIRICHLET for E_z) on all four walls,
+    C_CFL = 0.8, m = 3..6.  The L2 error of E_z against the exact mode falls with the grid
+    at high order and ends small, as the paper's Maxwell figure shows."""
+    from paper_1808_10481_gb300 import build, hl
+    build.build()
+    hl.load()
+    L, T = 0.5, 0.125
+    errs, Ns = [], [24, 32, 48]
+    for N in Ns:
+        h = L / N
+        steps = math.ceil(T / (0.8 * h))
+        dt = T / steps
+        p0, u0 = _tm_mode(m, N, L, 0.0, 0.5 * dt)
+        s = W.WalledSolver(2, m, [N, N], dt, ["dirichlet", "dirichlet"], length=[L, L])
+        try:
+            s.set_initial(p0, u0)
+            s.step(steps)
+            got_p, _ = s.fields()
+        finally:
+            s.close()
+        ex, _ = _tm_mode(m, N, L, steps * dt, (steps + 0.5) * dt)
+        errs.append(math.sqrt(h * h * float(np.sum((got_p[:, 0] - ex[:, 0]) ** 2))))
+    rate = float(np.polyfit(np.log(1.0 / np.array(Ns)), np.log(errs), 1)[0])
+    print(f"Maxwell TM m={m}: L2 errors {errs}, rate {rate:.2f}")
+    assert rate >= 2 * m - 1, (m, rate, errs)
+    assert errs[-1] < {3: 1e-7, 4: 1e-7, 5: 1e-10, 6: 1e-12}[m], (m, errs)
+
+
+@pytest.mark.gpu
+def test_walls_in_graph_mode_and_tc_split_match_fp64_steps():
+    """The ghost fill is stream-ordered: the same walled run captured as one CUDA graph, and
+    run with the tensor-core split contraction, matches the FP64 launches (the split mode
+    within its error bound)."""
+    from paper_1808_10481_gb300 import build, hl
+    build.build()
+    hl.load()
+    m, N, L = 3, 40, 0.5
+    dt = 0.8 * L / N
+    p0, u0 = _tm_mode(m, N, L, 0.0, 0.5 * dt, a=2, b=3)
+    out = {}
+    for name, graph, prec in (("plain", 0, hl.HL_FP64), ("graph", 1, hl.HL_FP64), ("tc", 0, hl.HL_TC_SPLIT)):
+        s = W.WalledSolver(2, m, [N, N], dt, ["dirichlet", "neumann"], length=[L, L])
+        try:
+            hl.hl_set_option(s.h, hl.HL_OPT_GRAPH, graph)
+            hl.hl_set_precision(s.h, prec)
+            s.set_initial(p0, u0)
+            s.step(30)
+            out[name] = s.fields()
+        finally:
+            s.close()
+    np.testing.assert_array_equal(out["graph"][0], out["plain"][0])
+    np.testing.assert_array_equal(out["graph"][1], out["plain"][1])
+    assert _rel(out["tc"][0], out["plain"][0]) < 1e-10 and _rel(out["tc"][1], out["plain"][1]) < 1e-10
