@@ -40,6 +40,7 @@
 // run per SM, so one CTA's cutting overlaps the other's MMAs.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 
 #include "hl_fp64.cuh"
@@ -94,12 +95,15 @@ __device__ __forceinline__ int64_t t5_fixed(double v, int emax)
     return x + 0x8080808080ll;
 }
 
-// digit i (most significant first) of a biased fixed-point value, as an exact float
+// digit i (most significant first) of a biased fixed-point value, as an exact float:
+// byte (5 - i) of y placed under the exponent of 2^23 by one byte permutation, then
+// (2^23 + byte) - (2^23 + 128)
 __device__ __forceinline__ float t5_digit(int64_t y, int i)
 {
     if (i == 0) return __uint_as_float(0x4B000000u + (uint32_t)((int)(y >> 40) + 256)) - 8388864.0f;
-    const uint32_t u = (uint32_t)((uint64_t)y >> (8 * (5 - i))) & 0xFFu;
-    return __uint_as_float(0x4B000000u | u) - 8388736.0f;  // (2^23 + u) - (2^23 + 128)
+    const int k = 5 - i;  // byte of y: 0..3 in the low word, 4 in the high word
+    const uint32_t w = k < 4 ? (uint32_t)y : (uint32_t)((uint64_t)y >> 32);
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (uint32_t)(k & 3))) - 8388736.0f;
 }
 
 // BF16 bits of two small-integer floats (exact: at most 8 significant bits)
@@ -357,6 +361,360 @@ __global__ void __launch_bounds__(kT5Threads, 2)
     if (warp == 0) tmem_dealloc(tmem, Op::TCOLS);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised form (the one the library launches): one CTA per
+// SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; per tile and
+// partner component ("unit") the roles hand data along mbarriers:
+//   producers (warps 0..PW-1): load their region rows, take the tile's exponent,
+//     cut the component into its digit planes in one of kT6Stages shared-memory
+//     stages  -> a_full[stage]
+//   MMA (warp PW, one lane): per unit 24 tcgen05.mma into one of two TMEM
+//     accumulators  -> a_empty[stage] (stage free), acc_full[acc] after the
+//     tile's last unit
+//   epilogue (the EW warps after it, EW/4 per TMEM lane quarter: one node per
+//     thread, the node's outputs split between the quarter's warps): the node's own
+//     values are loaded ahead (the first group while the MMAs run, the next while
+//     the current one is combined); levels to float-float, scaled, added to the
+//     binary64 node data  -> acc_empty[acc]
+// so that a tile's cutting overlaps the previous tiles' MMAs and epilogue.
+// The two half-steps balance the roles differently: the p-half reads two partner
+// components and writes one (9 producer warps, one region row a thread; 4 epilogue
+// warps), the u-half reads one and writes two (7 producer warps, rows t and t + 224
+// for t < 34; 8 epilogue warps).  Both stay at 128 registers a thread: the register
+// file is split between the SM's four sub-partitions, so 14 and 16 warps get the same.
+// The tile exponent travels through a ring of kT6ERing slots (e_full).
+// Every wait is bounded: on expiry a thread sets the abort flag and the
+// status bit, and all roles leave their loops (producers decide together at
+// their per-tile barrier); the MMA lane then waits for its MMAs in flight
+// before the tensor memory is released.
+template <bool PHALF>
+struct T6Roles {
+    static constexpr int PW = PHALF ? 9 : 7;          // producer warps
+    static constexpr int NPROD = PW * 32;
+    static constexpr int MMA = PW;                    // MMA warp
+    static constexpr int EPI0 = PW + 1;               // first epilogue warp
+    static constexpr int EW = PHALF ? 4 : 8;          // epilogue warps
+    static constexpr int THREADS = (PW + 1 + EW) * 32;
+    static constexpr int NSPLIT = EW / 4;             // warps per TMEM lane quarter
+    static constexpr int NGRP = (PHALF ? 2 : 4) / NSPLIT;   // 8-column groups a thread
+    static_assert(THREADS <= 512 && 2 * NPROD >= kT5Rows && NGRP * NSPLIT == (PHALF ? 2 : 4), "role layout");
+};
+constexpr int kT6MaxProdWarps = 9;
+constexpr int kT6Stages = 3;
+constexpr int kT6ERing = 8;
+constexpr int kT6BarBytes = 8 * (2 * kT6Stages + 2 + 2 + kT6ERing + 1);
+constexpr int kT6SmemBytes = kT5BBytes + kT6Stages * kT5ABytes + kT6BarBytes + 4 * (kT6ERing + 2 * kT6MaxProdWarps + 4);
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];\n" : "=l"(state) : "r"(mbar) : "memory");
+    (void)state;
+}
+
+// barrier 1 among the NPROD producer threads with an OR of a predicate over them
+template <int NPROD>
+__device__ __forceinline__ bool producers_sync_or(bool p)
+{
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}\n"
+        : "=r"(out)
+        : "r"((uint32_t)p), "n"(NPROD)
+        : "memory");
+    return out != 0;
+}
+
+// the shot of tile t (the last shot whose first tile is <= t)
+__device__ __forceinline__ void t6_tile(const ShotDesc *__restrict__ shots, int n_shots, int t, ShotDesc &sd, int &x0,
+                                        int &y)
+{
+    int lo = 0, hi = n_shots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (shots[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    sd = shots[lo];
+    const int tt = t - sd.tile_begin;
+    x0 = (tt % sd.tiles[0]) * kT5TileX;
+    y = tt / sd.tiles[0];
+}
+
+template <int M, bool PHALF>
+__global__ void __launch_bounds__(T6Roles<PHALF>::THREADS, 1)
+    k_half_tc6(const double *__restrict__ S, double *__restrict__ X, const ShotDesc *__restrict__ shots, int n_shots,
+               int total_tiles, const uint4 *__restrict__ Bimg, const int *__restrict__ expo, unsigned *status)
+{
+    constexpr int NQ = (M + 1) * (M + 1);
+    constexpr int NCIN = PHALF ? 2 : 1;
+    using Op = T5Op<PHALF>;
+    using R = T6Roles<PHALF>;
+    extern __shared__ __align__(1024) unsigned char t6_sm[];
+    unsigned char *Bs = t6_sm;
+    unsigned char *As = t6_sm + kT5BBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(As + kT6Stages * kT5ABytes);
+    uint64_t *a_full = bars, *a_empty = bars + kT6Stages, *acc_full = bars + 2 * kT6Stages,
+             *acc_empty = acc_full + 2, *e_full = acc_empty + 2, *drain = e_full + kT6ERing;
+    int *tileE = reinterpret_cast<int *>(drain + 1);
+    int *red = tileE + kT6ERing;                 // [2][R::PW]
+    volatile int *abort_flag = red + 2 * kT6MaxProdWarps;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(red + 2 * kT6MaxProdWarps + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tmem_alloc(smem_addr(tmem_slot), 2 * Op::TCOLS);
+        tc_fence_before();
+    }
+    if (tid == 32) {
+        for (int s = 0; s < kT6Stages; ++s) {
+            mbar_init(smem_addr(a_full + s), R::NPROD);
+            mbar_init(smem_addr(a_empty + s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_addr(acc_full + a), 1);
+            mbar_init(smem_addr(acc_empty + a), R::EW * 32);
+        }
+        for (int r = 0; r < kT6ERing; ++r) mbar_init(smem_addr(e_full + r), 1);
+        mbar_init(smem_addr(drain), 1);
+        *abort_flag = 0;
+    }
+    for (int e = tid; e < kT5BBytes / 16; e += R::THREADS) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(Bimg + e);
+    for (int e = tid; e < kT6Stages * kT5Digits * 2 * (kT5RowsPad - kT5Rows); e += R::THREADS) {
+        const int per = 2 * (kT5RowsPad - kT5Rows);
+        const int st = e / (kT5Digits * per), dg = (e / per) % kT5Digits, ch = (e / (kT5RowsPad - kT5Rows)) % 2;
+        const int r = kT5Rows + e % (kT5RowsPad - kT5Rows);
+        *reinterpret_cast<uint4 *>(As + st * kT5ABytes + dg * kT5Plane + ch * kT5Chunk + r * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int lo = PHALF ? -1 : 0;
+
+    if (warp < R::PW) {
+        // ------------------------------------------------------------ producers
+        const bool one = tid < kT5Rows;                 // a first region row
+        const bool two = tid + R::NPROD < kT5Rows;      // a second region row
+        const int r0 = one ? tid : 0, r1 = tid + R::NPROD;
+        int u = 0, lt = 0;
+        bool dead = false;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+            ShotDesc sd;
+            int x0, y;
+            t6_tile(shots, n_shots, t, sd, x0, y);
+            const int64_t nnode = sd.nnode;
+            const double *Sb = S + (PHALF ? sd.u_off : sd.p_off);
+            auto region_node = [&](int r) -> int64_t {
+                int gx = (x0 + lo + r % kT5RX) % sd.n[0];
+                if (gx < 0) gx += sd.n[0];
+                int gy = (y + lo + r / kT5RX) % sd.n[1];
+                if (gy < 0) gy += sd.n[1];
+                return gx + (int64_t)sd.n[0] * gy;
+            };
+            const int64_t nd0 = region_node(r0);
+            const int64_t nd1 = two ? region_node(r1) : nd0;
+            // the first row's first component stays in registers for its cut; everything
+            // else is read for its exponent now and again when it is cut (from L1/L2)
+            double v0[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v0[q] = __ldg(Sb + (int64_t)q * nnode + nd0);
+            int emax = 0;
+            bool bad = false;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int e0 = (__double2hiint(v0[q]) >> 20) & 0x7FF;
+                bad |= e0 == 0x7FF;
+                emax = max(emax, e0 == 0x7FF ? 0 : e0);
+            }
+#pragma unroll
+            for (int e = NQ; e < NCIN * NQ; ++e) {
+                const int e0 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd0)) >> 20) & 0x7FF;
+                bad |= e0 == 0x7FF;
+                emax = max(emax, e0 == 0x7FF ? 0 : e0);
+            }
+            if (two) {
+                for (int e = 0; e < NCIN * NQ; ++e) {
+                    const int e1 = (__double2hiint(__ldg(Sb + (int64_t)e * nnode + nd1)) >> 20) & 0x7FF;
+                    bad |= e1 == 0x7FF;
+                    emax = max(emax, e1 == 0x7FF ? 0 : e1);
+                }
+            }
+            report_nonfinite(bad, status);
+            emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+            if (lane == 0) red[(lt & 1) * R::PW + warp] = emax;
+            if (producers_sync_or<R::NPROD>(dead || *abort_flag != 0)) break;   // uniform over the producers
+#pragma unroll
+            for (int w = 0; w < R::PW; ++w) emax = max(emax, red[(lt & 1) * R::PW + w]);
+            if (tid == 0) {
+                tileE[lt % kT6ERing] = emax;
+                mbar_arrive(smem_addr(e_full + lt % kT6ERing));
+            }
+#pragma unroll
+            for (int c = 0; c < NCIN; ++c, ++u) {
+                const int st = u % kT6Stages;
+                if (dead) continue;
+                if (u >= kT6Stages &&
+                    !mbar_wait(smem_addr(a_empty + st), (uint32_t)(((u / kT6Stages) - 1) & 1), kT5WaitLimit)) {
+                    dead = true;
+                    *abort_flag = 1;
+                    atomicOr(status, kStatusTimeout);
+                    continue;
+                }
+                if (c > 0) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) v0[q] = __ldg(Sb + (int64_t)(c * NQ + q) * nnode + nd0);
+                }
+                if (one) t5_store_row_regs<NQ>(As + st * kT5ABytes, r0, v0, emax);
+                if (two) t5_store_row<NQ>(As + st * kT5ABytes, r1, Sb + (int64_t)c * NQ * nnode + nd1, nnode, emax);
+                fence_async_smem();
+                mbar_arrive(smem_addr(a_full + st));
+            }
+        }
+    } else if (warp == R::MMA) {
+        // ------------------------------------------------------------ MMA issue (one lane)
+        if (lane == 0) {
+            const uint32_t b0 = smem_addr(Bs);
+            int u = 0, lt = 0;
+            for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+                if (*abort_flag) break;
+                const int ac = lt & 1;
+                if (lt >= 2 && !mbar_wait(smem_addr(acc_empty + ac), (uint32_t)(((lt >> 1) - 1) & 1), kT5WaitLimit)) {
+                    *abort_flag = 1;
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                tc_fence_after();
+                bool ok = true;
+                for (int c = 0; c < NCIN; ++c, ++u) {
+                    const int st = u % kT6Stages;
+                    if (!mbar_wait(smem_addr(a_full + st), (uint32_t)((u / kT6Stages) & 1), kT5WaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_addr(As + st * kT5ABytes);
+#pragma unroll
+                    for (int i = 0; i < kT5Digits; ++i) {
+                        const int nlev = i == 0 ? kT5Levels : min(kT5Digits, kT5Levels - i);
+                        const uint32_t idesc = umma_idesc_bf16(128, Op::NPL * nlev);
+#pragma unroll
+                        for (int vtx = 0; vtx < 4; ++vtx) {
+                            const uint32_t arow = (uint32_t)((vtx >> 1) * kT5RX + (vtx & 1));
+                            const uint64_t ad = umma_desc(a0 + (uint32_t)(i * kT5Plane) + arow * 16u, kT5Chunk, 128);
+                            const int kb = PHALF ? c * 4 + vtx : vtx;
+                            const uint64_t bd = umma_desc(b0 + (uint32_t)(kb * Op::KB_BYTES), Op::NROWS * 16, 128);
+                            umma_bf16(tmem + (uint32_t)(ac * Op::TCOLS + Op::NPL * i), ad, bd, idesc,
+                                      (c | i | vtx) != 0 ? 1u : 0u);
+                        }
+                    }
+                    umma_commit(smem_addr(a_empty + st));
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                umma_commit(smem_addr(acc_full + ac));
+            }
+            // every MMA issued has completed before the tensor memory is released
+            umma_commit(smem_addr(drain));
+            mbar_wait(smem_addr(drain), 0u, kT5WaitLimit);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;                 // the TMEM lanes a warp may read
+        const int half = (warp - R::EPI0) >> 2;       // which share of the node's outputs
+        const int q = 32 * quarter + lane;            // node within the tile = TMEM lane
+        const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
+        constexpr int NGRP = R::NGRP;                 // groups of 8 output columns per thread
+        int lt = 0;
+        bool bad = false;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+            if (*abort_flag) break;
+            ShotDesc sd;
+            int x0, y;
+            t6_tile(shots, n_shots, t, sd, x0, y);
+            const int64_t nnode = sd.nnode;
+            double *Xb = X + (PHALF ? sd.p_off : sd.u_off);
+            const int gx = x0 + q;
+            const bool mine = gx < sd.n[0];
+            const int64_t node = (int64_t)gx + (int64_t)sd.n[0] * y;
+            const int ac = lt & 1;
+            auto load_own = [&](int g, double *own) {
+                const int cg = NGRP * half + g;  // column group of the level
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int s = (8 * cg + j) % 16, oc = (8 * cg + j) / 16;
+                    own[j] = (mine && s < NQ) ? Xb[(int64_t)(oc * NQ + s) * nnode + node] : 0.0;
+                }
+            };
+            double own[8], nxt[8];
+            load_own(0, own);  // in flight while this tile's MMAs run
+            if (!mbar_wait(smem_addr(e_full + lt % kT6ERing), (uint32_t)((lt / kT6ERing) & 1), kT5WaitLimit) ||
+                !mbar_wait(smem_addr(acc_full + ac), (uint32_t)((lt >> 1) & 1), kT5WaitLimit)) {
+                *abort_flag = 1;
+                atomicOr(status, kStatusTimeout);
+                break;
+            }
+            tc_fence_after();
+            const int E = tileE[lt % kT6ERing] - 1022;
+#pragma unroll
+            for (int g = 0; g < NGRP; ++g) {
+                const int col0 = 8 * (NGRP * half + g);  // within a level: component col0 / 16
+                if (g + 1 < NGRP) load_own(g + 1, nxt);
+                // levels summed from the smallest weight up, in two batches of TMEM loads
+                FF tot[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) tot[j] = FF{0.f, 0.f};
+#pragma unroll
+                for (int batch = 0; batch < 2; ++batch) {
+                    constexpr int kHi = kT5Levels - 1;
+                    const int Lhi = batch == 0 ? kHi : 2, Llo = batch == 0 ? 3 : 0;
+                    float accv[4][8];
+#pragma unroll
+                    for (int L = Lhi; L >= Llo; --L)
+                        tmem_ld8(tl + (uint32_t)(ac * Op::TCOLS + L * Op::NPL + col0), accv[Lhi - L]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int L = Lhi; L >= Llo; --L)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float val = accv[Lhi - L][j] * __uint_as_float((uint32_t)(127 - 8 * L) << 23);
+                            const FF s2 = ff_two_sum(tot[j].hi, val);
+                            tot[j].hi = s2.hi;
+                            tot[j].lo = __fadd_rn(tot[j].lo, s2.lo);
+                        }
+                }
+                if (mine) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int s = (col0 + j) % 16, oc = (col0 + j) / 16;
+                        if (s >= NQ) continue;
+                        const FF nrm = ff_two_sum(tot[j].hi, tot[j].lo);
+                        const int k0 = E + __ldg(expo + oc * 16 + s) - 14;
+                        const double inc = t5_scaled_f64(nrm.hi, k0) + t5_scaled_f64(nrm.lo, k0);
+                        const double nv = own[j] + inc;
+                        Xb[(int64_t)(oc * NQ + s) * nnode + node] = nv;
+                        bad |= nonfinite(nv);
+                    }
+                }
+                if (g + 1 < NGRP) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) own[j] = nxt[j];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_addr(acc_empty + ac));
+        }
+        report_nonfinite(bad, status);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 2 * Op::TCOLS);
+}
+
 template <int M>
 static cudaError_t run_tc5(const LaunchFp64 &a)
 {
@@ -367,27 +725,29 @@ static cudaError_t run_tc5(const LaunchFp64 &a)
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(opted_in.load() & bit)) {
-        if ((e = cudaFuncSetAttribute(k_half_tc5<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kT5SmemBytes)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_half_tc5<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kT5SmemBytes)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_half_tc6<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kT6SmemBytes)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_half_tc6<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kT6SmemBytes)) != cudaSuccess)
             return e;
         opted_in.fetch_or(bit);
     }
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     constexpr int NQ = (M + 1) * (M + 1);
     const uint4 *bp = reinterpret_cast<const uint4 *>(a.tc_digits);
     const uint4 *bu = reinterpret_cast<const uint4 *>(a.tc_digits + kT5BBytes / 2);
-    const dim3 grid((unsigned)a.tc_tiles);
+    const dim3 grid((unsigned)std::min(a.tc_tiles, sms));  // persistent: one CTA per SM
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        k_half_tc5<M, true><<<grid, kT5Threads, kT5SmemBytes, a.stream>>>(a.U, a.P, a.tc_shots, a.n_shots, bp,
-                                                                          a.tc_expo, a.status);
+        k_half_tc6<M, true><<<grid, T6Roles<true>::THREADS, kT6SmemBytes, a.stream>>>(a.U, a.P, a.tc_shots, a.n_shots,
+                                                                          a.tc_tiles, bp, a.tc_expo, a.status);
         if (a.src && a.src->active) {
             if ((e = launch_source(*a.src, a.shots, a.P, NQ, a.step0 + st, a.stream)) != cudaSuccess) return e;
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
-        k_half_tc5<M, false><<<grid, kT5Threads, kT5SmemBytes, a.stream>>>(a.P, a.U, a.tc_shots, a.n_shots, bu,
-                                                                           a.tc_expo + 16, a.status);
+        k_half_tc6<M, false><<<grid, T6Roles<false>::THREADS, kT6SmemBytes, a.stream>>>(a.P, a.U, a.tc_shots, a.n_shots,
+                                                                           a.tc_tiles, bu, a.tc_expo + 16, a.status);
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();
