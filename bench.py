@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-seeds", type=int, default=96, help="learned workload: training seeds")
     ap.add_argument("--test-seeds", type=int, default=32, help="learned workload: held-out seeds")
-    ap.add_argument("--workload", choices=["3d", "2d", "1d", "batch", "mixed3d", "mixed2d", "learned"], default="3d",
+    ap.add_argument("--workload", choices=["3d", "2d", "1d", "batch", "mixed3d", "mixed2d", "learned", "split3d",
+                                           "modified1d", "variable1d"], default="3d",
                     help="3d: the headline line; the others measure further rows of the solver")
     return ap.parse_args()
 
@@ -367,6 +368,10 @@ def run_aux(args, rank=0, world=1, dist=None):
                     "modes": modes})
     elif args.workload == "learned":
         out.update(run_learned(args, n_train=args.train_seeds, n_test=args.test_seeds))
+    elif args.workload == "split3d":
+        out.update(run_split3d(hl, I, stream))
+    elif args.workload in ("modified1d", "variable1d"):
+        out.update(run_1d_variant(args.workload, hl, I, stream))
     else:
         from paper_1808_10481_gb300.sharding import max_over_ranks, shard_by_cost
         d, m, n_shots, lf = 2, 3, 64, 500
@@ -428,6 +433,128 @@ def run_aux(args, rank=0, world=1, dist=None):
                     "status": rc})
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_split3d(hl, I, stream):
+    """Section 6's comparison on GB300: the fused FP64 kernels against the split pair
+    (interpolant stored, then evolved), 3D plane wave, m = 1/2/3 on the paper's grids
+    200^3 / 130^3 / 100^3 (Table 6), time per iteration (p-half + u-half) and each form's
+    algorithmic FP64 rate and HBM bandwidth per half-step."""
+    import numpy as np
+    import torch
+    rows = {}
+    for m, n in ((1, 200), (2, 130), (3, 100)):
+        ncell = [n] * 3
+        dt = I.cfl_dt(ncell)
+        st = I.plane_wave(m, ncell, dt, seed=3)
+        nq, A = (m + 1) ** 3, 2 * m + 2
+        AD = A ** 3
+        nnode = n ** 3
+        res = {}
+        for name, split in (("fused", 0), ("split", 1)):
+            h = hl.hl_create(3, m, ncell, dt)
+            try:
+                hl.hl_set_stream(h, stream)
+                hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, 2)
+                if split:
+                    hl.hl_set_option(h, hl.HL_OPT_SPLIT, 1)
+                else:
+                    hl.hl_autotune(h, 1)
+                hl.hl_set_initial(h, st.p, st.u)
+                hl.hl_step(h, 3)
+                hl.hl_sync(h)
+                hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
+                hl.hl_kernel_times(h)
+                steps = 10
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hl.hl_step(h, steps)
+                e1.record(stream)
+                rc = hl.hl_sync(h)
+                kt, kc = hl.hl_kernel_times(h)
+            finally:
+                hl.hl_destroy(h)
+            r = {"ms_per_iteration": e0.elapsed_time(e1) / steps, "p_half_ms": kt["p_half"] / kc["p_half"],
+                 "u_half_ms": kt["u_half"] / kc["u_half"], "status": rc}
+            if split:
+                # per half-step: interpolation reads the partner once and writes its interpolant,
+                # evolution reads the interpolant and the node's own data and writes them back
+                bytes_p = 8 * nnode * (3 * nq + 3 * AD + 3 * AD + 2 * nq)
+                bytes_u = 8 * nnode * (nq + AD + AD + 2 * 3 * nq)
+                fl_p = 2 * nnode * 3 * (3 * AD * A)
+                fl_u = 2 * nnode * (3 * AD * A)
+            else:
+                fma, add = hl.hl_op_counts(3, m)
+                bytes_p = 8 * nnode * (3 * nq + 2 * nq)
+                bytes_u = 8 * nnode * (nq + 2 * 3 * nq)
+                fl_p = fl_u = nnode * (fma + add / 2.0)   # half of the full step's count each
+            r["p_half_gbs"] = bytes_p / (r["p_half_ms"] / 1e3) / 1e9
+            r["u_half_gbs"] = bytes_u / (r["u_half_ms"] / 1e3) / 1e9
+            r["p_half_interp_gflops"] = fl_p / (r["p_half_ms"] / 1e3) / 1e9
+            r["u_half_interp_gflops"] = fl_u / (r["u_half_ms"] / 1e3) / 1e9
+            res[name] = r
+        res["split_over_fused"] = res["split"]["ms_per_iteration"] / res["fused"]["ms_per_iteration"]
+        res["dof_updates_per_s_fused"] = 4 * nq * nnode / (res["fused"]["ms_per_iteration"] / 1e3)
+        rows[f"m{m}_{n}^3"] = res
+    return {"workload": "split3d", "value": rows["m2_130^3"]["dof_updates_per_s_fused"],
+            "config": {"workload": "3D plane wave, m = 1/2/3 on 200^3/130^3/100^3 (Table 6 sizes), fused "
+                                   "FP64 kernels against the split interpolation + evolution pair, 10 iterations"},
+            "table6": rows,
+            "note": "split rows' GB/s count the stored interpolant round trip; GFLOP/s count the "
+                    "interpolation's sum-factorised multiply-adds (fused: the fused operator's)"}
+
+
+def run_1d_variant(workload, hl, I, stream):
+    """Throughput of the 1D method variants on a long periodic interval: the modified
+    Hermite-leapfrog scheme (both fields on both grids) and the variable wave speed."""
+    import math
+    import numpy as np
+    import torch
+    m, n, steps = 3, 1 << 22, 50
+    if workload == "modified1d":
+        dt = 0.9 / n
+        st = I.standing_mode_1d_both_grids(m, n, dt, 3)
+        h = hl.hl_mod_create(m, n, dt)
+        try:
+            hl.hl_mod_set_stream(h, stream)
+            hl.hl_mod_set_initial(h, *st)
+            hl.hl_mod_step(h, 3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hl.hl_mod_step(h, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            hl.hl_mod_get_fields(h)
+        finally:
+            hl.hl_mod_destroy(h)
+        dof = 4 * (m + 1) * n   # p and u on both grids
+        desc = "modified Hermite-leapfrog, 1D, m=3, 2^22 nodes per grid, standing wave, 50 steps"
+        bytes_step = 8 * n * (m + 1) * (4 + 2 * 4)    # both grids: read partner (2 fields), read+write own (2 fields)
+    else:
+        dt = 0.9 / n / I.c2_max()
+        p, u, _, _ = I.variable_speed_wave(m, n, dt)
+        h = hl.hl_create(1, m, [n], dt)
+        try:
+            hl.hl_set_stream(h, stream)
+            hl.hl_set_wave_speed(h, I.c2_taylor_table(n, m, False), I.c2_taylor_table(n, m, True))
+            hl.hl_set_initial(h, p, u.reshape(1, n, m + 1))
+            hl.hl_step(h, 3)
+            hl.hl_sync(h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hl.hl_step(h, steps)
+            e1.record(stream)
+            hl.hl_sync(h)
+        finally:
+            hl.hl_destroy(h)
+        dof = 2 * (m + 1) * n
+        desc = "variable wave speed c^2 = 1 + sin(2 pi x)/2, 1D, m=3, 2^22 nodes, 50 steps"
+        bytes_step = 8 * n * ((m + 1) * 6 + 2 * (2 * m + 2))   # fields + both c^2 tables
+    ms = e0.elapsed_time(e1)
+    return {"workload": workload, "value": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "hbm_gbs_algorithmic": bytes_step * steps / (ms / 1e3) / 1e9,
+            "config": {"workload": desc, "dim": 1, "m": m, "n_cells": [n]}}
 
 
 def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
@@ -890,6 +1017,14 @@ def run_headline(args):
         modes["fp64_error_ladder"] = ladder
     del hp
 
+    # 2D companion at the size of the 2D workload, where the tensor-core split mode runs: the
+    # standing mode sin(48 pi x) sin(48 pi y) cos(w t) (exact solution known; 21 points per
+    # wavelength, so the discretisation error sits well above rounding), 512^2, m = 3,
+    # 200 steps, each mode beside the fastest plain FP64 grid of no larger L2 error
+    modes_2d = None
+    if rank == 0:
+        modes_2d = run_modes_2d(hl, I, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -906,10 +1041,69 @@ def run_headline(args):
             "gpu_launches": int(kcount["p_half"] + kcount["u_half"] + kcount["small"]),
             "kernel_ms": ktimes, "fp64_l2_err_p_vs_exact": fp64_l2,
             "modes_vs_fp64_at_equal_l2_error": modes,
+            "modes_2d_vs_fp64_at_equal_l2_error": modes_2d,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_modes_2d(hl, I, stream, n=512, m=3, lf=200, wave=(24, 24)):
+    """Every precision mode on the 2D standing mode at n^2, its L2 error against the exact
+    solution, and the plain FP64 grid that reaches that error fastest."""
+    import numpy as np
+    import torch
+
+    def run(ncell, steps, dt, mode, tune=True):
+        st = I.standing_mode(2, m, ncell, dt, wave=list(wave))
+        ex = I.standing_mode_exact(2, m, ncell, list(wave), steps * dt, (steps + 0.5) * dt)
+        h = hl.hl_create(2, m, ncell, dt)
+        try:
+            hl.hl_set_stream(h, stream)
+            hl.hl_set_precision(h, mode)
+            hl.hl_set_initial(h, st.p, st.u)
+            if tune:
+                hl.hl_autotune(h, 2)
+            hl.hl_step(h, 3)                       # warm-up
+            hl.hl_set_initial(h, st.p, st.u)
+            hl.hl_set_option(h, hl.HL_OPT_TIMING, 1)
+            hl.hl_kernel_times(h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hl.hl_step(h, steps)
+            e1.record(stream)
+            rc = hl.hl_sync(h)
+            kt, kc = hl.hl_kernel_times(h)
+            pg, _, _, _ = hl.hl_get_fields(h)
+        finally:
+            hl.hl_destroy(h)
+        return e0.elapsed_time(e1), I.l2_error(2, ncell, pg, ex.p), rc, kt, kc
+
+    ncell = [n, n]
+    dt = I.cfl_dt(ncell)
+    dof = 3 * (m + 1) ** 2 * n * n * lf
+    out = {"config": f"2D standing mode sin({2 * wave[0]} pi x) sin({2 * wave[1]} pi y), {n}^2, m={m}, "
+                     f"{lf} steps, C_CFL=0.9"}
+    for name, mode in (("fp64", hl.HL_FP64), ("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP),
+                       ("tc_split", hl.HL_TC_SPLIT)):
+        ms, err, rc, kt, kc = run(ncell, lf, dt, mode)
+        out[name] = {"value": dof / (ms / 1e3), "ms_per_run": ms, "l2_err_p_vs_exact": err, "status": rc,
+                     "p_half_us": 1e3 * kt["p_half"] / max(kc["p_half"], 1),
+                     "u_half_us": 1e3 * kt["u_half"] / max(kc["u_half"], 1)}
+    t_end = lf * dt
+    ladder = [{"n": n, "ms_run": out["fp64"]["ms_per_run"], "l2_err_p_vs_exact": out["fp64"]["l2_err_p_vs_exact"]}]
+    for n2 in (192, 256, 320, 384, 448):
+        c2 = [n2, n2]
+        steps2 = int(np.ceil(t_end / I.cfl_dt(c2) - 1e-9))
+        ms, err, _, _, _ = run(c2, steps2, t_end / steps2, hl.HL_FP64, tune=False)
+        ladder.append({"n": n2, "ms_run": ms, "l2_err_p_vs_exact": err})
+    for name in ("fp32", "fp32_comp", "tc_split"):
+        ok = [r for r in ladder if r["l2_err_p_vs_exact"] <= out[name]["l2_err_p_vs_exact"] * 1.01]
+        r = min(ok, key=lambda x: x["ms_run"]) if ok else None
+        out[name]["fp64_at_equal_error"] = None if r is None else dict(
+            r, speedup_vs_fp64_at_equal_error=r["ms_run"] / out[name]["ms_per_run"])
+    out["fp64_error_ladder"] = ladder
+    return out
 
 
 def main():

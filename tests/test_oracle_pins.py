@@ -372,8 +372,11 @@ def _check_rate(m, got, paper):
         # even orders: the paper observes (and the dispersion analysis explains) 2m+2
         assert abs(got - paper) <= 0.35, (m, got, paper)
     else:
-        # odd orders: at least the proven 2m, with the variation the paper reports
-        assert 2 * m - 0.5 <= got <= 2 * m + 3.5, (m, got, paper)
+        # odd orders: the proven 2m (Section 3.2) up to the pre-asymptotic excess the
+        # paper's tables show; the local rates between successive grids oscillate
+        # (2D m = 3 at T = 0.5: 4.5 to 6.8 on 8..32 nodes, 5.9 to 6.0 beyond), so the
+        # fitted rate depends on the grid range, which the paper does not state for 2D
+        assert 2 * m - 0.5 <= got <= 2 * m + 1.5, (m, got, paper)
 
 
 @pytest.mark.parametrize("cfl,table", [(0.9, "table1_rates_cfl09.txt"), (0.5, "table1_rates_cfl05.txt"),
@@ -621,3 +624,23 @@ def test_adam_is_invariant_to_gradient_scale_without_eps():
             mlp.adam_step(w, {"a": scale * g["a"]}, m1, m2, t, 0.01, eps=0.0)
         out.append(w["a"])
     np.testing.assert_allclose(out[0], out[1], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_2d_odd_order_local_rates_settle_at_2m(m):
+    """Odd orders in 2D: the local rates log(e_N / e_2N) / log 2 between successive finer grids
+    settle at the proven 2m (Section 3.2's h^(2m) bound) once the grids resolve the mode; the
+    paper's larger odd entries of Table 5 (6.74, 7.45, 6.84 for m = 3) lie within the spread of
+    the pre-asymptotic local rates on coarse grids."""
+    Ns = [24, 32, 48, 64]
+    errs = []
+    for N in Ns:
+        ncell = [N, N]
+        n = math.ceil(2.065 / (0.9 / N))
+        dt = 2.065 / n
+        st = I.standing_mode(2, m, ncell, dt, wave=[1, 1])
+        p, _ = oracle.run(2, m, ncell, dt, st.p, st.u, n)
+        ex = I.standing_mode_exact(2, m, ncell, [1, 1], n * dt, (n + 0.5) * dt)
+        errs.append(I.l2_error(2, ncell, p, ex.p))
+    local = [math.log(errs[i] / errs[i + 1]) / math.log(Ns[i + 1] / Ns[i]) for i in range(len(Ns) - 1)]
+    assert all(abs(r - 2 * m) <= 0.3 for r in local), local
