@@ -3,9 +3,10 @@
 // with an iteration limit, and the shared-memory matrix descriptors.
 //
 // Conventions used by the kernels:
-//   - operands A (M x K) and B (N x K) are BF16, K-major, in shared memory in
-//     the no-swizzle canonical layout: a "core matrix" is 8 rows of 16 bytes
-//     (8 BF16 along K) stored contiguously (128 bytes); the descriptor's
+//   - operands A (M x K) and B (N x K) are 16-bit (BF16 or FP16, both the same),
+//     K-major, in shared memory in the no-swizzle canonical layout: a "core
+//     matrix" is 8 rows of 16 bytes (8 elements along K) stored contiguously
+//     (128 bytes); the descriptor's
 //     leading-dimension byte offset (LBO) is the distance between core
 //     matrices adjacent along K, the stride byte offset (SBO) the distance
 //     between core matrices adjacent along M (or N);
@@ -40,7 +41,15 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// D[tmem] (+)= A[smem] B[smem]^T, one instruction (K = 16 for BF16)
+// Instruction descriptor of tcgen05.mma.kind::f16: FP16 A and B (K-major),
+// FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] B[smem]^T, one instruction (K = 16 for BF16 or FP16;
+// the element type is the instruction descriptor's)
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                           uint32_t accumulate)
 {
