@@ -85,15 +85,18 @@ enum {
                             data and operator as binary32 hi + lo pairs and
                             float-float arithmetic throughout (error-free
                             TwoSum / TwoProduct), about 48 significant bits  */
-    HL_TC_SPLIT = 3      /* dim = 2 only: the contraction as exact BF16
-                            tensor-core products on the fifth-generation
-                            tensor cores (tcgen05.mma, FP32 accumulators in
-                            tensor memory): the binary64 node data of a
-                            128-node tile's region and the operator scaled
-                            by powers of two and cut into 6 base-256 digits;
-                            the digit pairs of the 7 leading levels are
-                            summed, each level exactly, then in float-float;
-                            about 46 bits below the block maximum        */
+    HL_TC_SPLIT = 3      /* dim = 2 (m <= 3) and dim = 3 (m = 2, one shot):
+                            the contraction as exact FP16 digit products on
+                            the fifth-generation tensor cores (tcgen05.mma,
+                            FP32 accumulators in tensor memory): the binary64
+                            partner data (scaled by the largest power of two
+                            of a 128-node tile's region in 2D, of the whole
+                            field in 3D) and the operator cut into 6
+                            base-256 digits; the digit pairs of the 7
+                            leading levels are summed, each level exactly,
+                            then in float-float; about 46 bits below that
+                            maximum.  3D allocates digit planes of both
+                            fields (1.5x the state's size)                  */
 };
 
 /*
@@ -284,9 +287,10 @@ int hl_autotune(hl_solver *h, int64_t steps_per_trial, int *best_tile, double *m
 
 /*
  * hl_set_precision -- select the arithmetic mode (HL_FP64, HL_FP32,
- * HL_FP32_COMP, HL_TC_SPLIT).  The mixed modes need m <= 3 (m <= 2 in 3D,
- * HL_TC_SPLIT dim = 2 only) and, on a batch, the same dt/h on every shot;
- * they return HL_EINVAL otherwise.  Takes effect at the next hl_step.
+ * HL_FP32_COMP, HL_TC_SPLIT).  The mixed modes need m <= 3 (m <= 2 in 3D;
+ * HL_TC_SPLIT: dim 2 or 3, in 3D m = 2 and a single shot) and, on a batch,
+ * the same dt/h on every shot; they return HL_EINVAL otherwise (HL_ENOMEM
+ * when the 3D digit planes do not fit).  Takes effect at the next hl_step.
  */
 int hl_set_precision(hl_solver *h, int mode);
 

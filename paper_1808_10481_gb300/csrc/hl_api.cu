@@ -82,6 +82,9 @@ static void release(hl_solver *h)
     if (h->tc_digits) cudaFree(h->tc_digits);
     if (h->tc_expo) cudaFree(h->tc_expo);
     if (h->tc_shots) cudaFree(h->tc_shots);
+    if (h->tc3_gu) cudaFree(h->tc3_gu);
+    if (h->tc3_gp) cudaFree(h->tc3_gp);
+    if (h->tc3_emax) cudaFree(h->tc3_emax);
     if (h->c2_primal) cudaFree(h->c2_primal);
     if (h->c2_dual) cudaFree(h->c2_dual);
     if (h->split_coef) cudaFree(h->split_coef);
@@ -277,8 +280,10 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
     if (rc) return rc;
     if (mode != HL_FP64 && mode != HL_FP32 && mode != HL_FP32_COMP && mode != HL_TC_SPLIT)
         return set_err(h, HL_EINVAL, "unknown precision mode");
-    if (mode == HL_TC_SPLIT && h->dim != 2)
-        return set_err(h, HL_EINVAL, "the tensor-core split mode supports dim = 2");
+    if (mode == HL_TC_SPLIT && h->dim == 1)
+        return set_err(h, HL_EINVAL, "the tensor-core split mode supports dim = 2 and 3");
+    if (mode == HL_TC_SPLIT && h->dim == 3 && (h->m != 2 || h->shots.size() != 1))
+        return set_err(h, HL_EINVAL, "the 3D tensor-core split mode supports m = 2 and one shot");
     if (mode != HL_FP64 && h->c2_primal)
         return set_err(h, HL_EINVAL, "a variable wave speed runs in HL_FP64 only");
     if (mode != HL_FP64 && h->split_coef)
@@ -306,7 +311,30 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
             if (!h->Ul) HL_CK(h, cudaMalloc(&h->Ul, n * h->dim * sizeof(float)));
         }
     }
-    if (mode == HL_TC_SPLIT && (!h->tc_digits || !h->tc_expo || !h->tc_shots)) {
+    if (mode == HL_TC_SPLIT && h->dim == 3 && (!h->tc_digits || !h->tc3_gu)) {
+        // 3D: operator images streamed per unit, digit planes of both fields
+        // (with periodic ghost columns and a tail the last tile's row copies may
+        // reach into), the fields' exponent words
+        std::vector<uint16_t> img;
+        std::vector<int> ex;
+        if (!build_tc3_images(h->m, h->coef.data(), img, ex))
+            return set_err(h, HL_EINVAL, "3D tensor-core tables need m = 2");
+        const Shot &sh = h->shots[0];
+        const size_t plane = (size_t)sh.n[1] * sh.n[2] * (sh.n[0] + 2);
+        const size_t ngu = 3 * 6 * 4 * plane + 256, ngp = 6 * 4 * plane + 256;
+        HL_CK(h, cudaStreamSynchronize(h->stream));
+        if (!h->tc_digits) HL_CK(h, cudaMalloc(&h->tc_digits, img.size() * sizeof(uint16_t)));
+        if (!h->tc_expo) HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
+        if (!h->tc3_emax) HL_CK(h, cudaMalloc(&h->tc3_emax, 2 * sizeof(int)));
+        if (!h->tc3_gu) HL_CK(h, cudaMalloc(&h->tc3_gu, ngu * sizeof(uint4)));
+        if (!h->tc3_gp) HL_CK(h, cudaMalloc(&h->tc3_gp, ngp * sizeof(uint4)));
+        HL_CK(h, cudaMemset(h->tc3_gu, 0, ngu * sizeof(uint4)));
+        HL_CK(h, cudaMemset(h->tc3_gp, 0, ngp * sizeof(uint4)));
+        HL_CK(h, cudaMemcpy(h->tc_digits, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        HL_CK(h, cudaMemcpy(h->tc_expo, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
+        h->tc_tiles = (int)(((sh.n[0] + kTc5TileX - 1) / kTc5TileX) * sh.n[1] * sh.n[2]);
+    }
+    if (mode == HL_TC_SPLIT && h->dim == 2 && (!h->tc_digits || !h->tc_expo || !h->tc_shots)) {
         // the tcgen05 kernels read the binary64 state directly: operator images,
         // their column exponents and a tile table of 128-node row tiles
         std::vector<uint16_t> img;
@@ -556,6 +584,9 @@ static LaunchFp64 launch_args(hl_solver *h, double *P, double *U, int64_t n_step
     a.tc_expo = h->tc_expo;
     a.tc_shots = h->tc_shots;
     a.tc_tiles = h->tc_tiles;
+    a.tc3_gu = h->tc3_gu;
+    a.tc3_gp = h->tc3_gp;
+    a.tc3_emax = h->tc3_emax;
     a.c2_primal = h->c2_primal;
     a.c2_dual = h->c2_dual;
     a.var_lam = h->shots[0].lam[0];
@@ -570,7 +601,7 @@ static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 {
     if (a.c2_primal) return dim == 1 ? launch_var_d1(a) : cudaErrorInvalidValue;
     if (a.split_coef && a.precision == HL_FP64) return launch_split(dim, a);
-    if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : cudaErrorInvalidValue;
+    if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : dim == 3 ? launch_tc_d3(a) : cudaErrorInvalidValue;
     if (a.precision != HL_FP64) {
         switch (dim) {
         case 1: return launch_mixed_d1(a);

@@ -84,6 +84,9 @@ struct LaunchFp64 {
     const int *tc_expo = nullptr;
     const ShotDesc *tc_shots = nullptr;
     int tc_tiles = 0;
+    // 3D: digit planes of the partner fields (hl_tc3.cu) and their exponent words
+    uint4 *tc3_gu = nullptr, *tc3_gp = nullptr;
+    int *tc3_emax = nullptr;
     // variable wave speed (dim = 1, one grid): device tables [i][node] of the scaled
     // Taylor coefficients of c^2 at the primal and dual nodes, i = 0..2m+1; dt/(2h)
     const double *c2_primal = nullptr;
@@ -113,6 +116,10 @@ bool build_tc_tables(int m, const double *coef, std::vector<uint16_t> &digits, s
 constexpr int kTc5ImageElems = 2 * 14336;
 bool build_tc5_images(int m, const double *coef, std::vector<uint16_t> &image, std::vector<int> &expo);
 constexpr int kTc5TileX = 128;  // nodes per tile of the tcgen05 kernels
+// 3D (m = 2) operator images (hl_tc3.cu): per half 12 units of 4 x 2 x 224 x 8 FP16
+constexpr int kTc3UnitElems = 4 * 2 * 224 * 8;
+constexpr int kTc3ImageElems = 2 * 12 * kTc3UnitElems;
+bool build_tc3_images(int m, const double *coef, std::vector<uint16_t> &image, std::vector<int> &expo);
 
 cudaError_t launch_fp64_d1(const LaunchFp64 &a);
 cudaError_t launch_fp64_d2(const LaunchFp64 &a);
@@ -121,6 +128,7 @@ cudaError_t launch_mixed_d1(const LaunchFp64 &a);  // precision 1 or 2, m <= 3
 cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
+cudaError_t launch_tc_d3(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m = 2, one shot
 cudaError_t launch_var_d1(const LaunchFp64 &a);    // variable wave speed, dim = 1, FP64
 cudaError_t launch_split(int dim, const LaunchFp64 &a);  // split two-kernel FP64 ablation, m <= 3
 // ghost planes of the walled axes (kinds: 0 periodic, 1 dirichlet, 2 neumann), in axis order

@@ -84,6 +84,8 @@ struct hl_solver {
     int *tc_expo = nullptr;         // and their column exponents
     hl::ShotDesc *tc_shots = nullptr;  // HL_TC_SPLIT tile table: 128-node tiles of one grid row
     int tc_tiles = 0;
+    uint4 *tc3_gu = nullptr, *tc3_gp = nullptr;  // 3D HL_TC_SPLIT: digit planes of u and p (hl_tc3.cu)
+    int *tc3_emax = nullptr;                     // and the fields' exponent words
     double *c2_primal = nullptr, *c2_dual = nullptr;  // variable wave speed tables (dim = 1), [i][node]
     // split two-kernel ablation (HL_OPT_SPLIT)
     double *split_coef = nullptr;

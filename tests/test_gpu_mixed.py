@@ -1,5 +1,5 @@
 """Mixed-precision modes: the contraction on the FP32 pipe (HL_FP32, HL_FP32_COMP) or
-as exact BF16 tensor-core digit products (HL_TC_SPLIT, 2D), the node data and their
+as exact FP16 tensor-core digit products (HL_TC_SPLIT, 2D and 3D), the node data and their
 updates in binary64.
 
 Their error against the FP64 oracle is stated and bounded by the arithmetic, not held to
@@ -270,13 +270,79 @@ def test_tc_split_batch_matches_each_shot_alone():
 
 
 def test_tc_split_validation():
-    for d, m, nc in ((3, 2, [4, 4, 4]), (1, 3, [16]), (2, 4, [8, 8])):
+    for d, m, nc in ((3, 1, [4, 4, 4]), (1, 3, [16]), (2, 4, [8, 8])):
         h = hl.hl_create(d, m, nc, 0.9 / max(nc))
         try:
             with pytest.raises(hl.HLError):
                 hl.hl_set_precision(h, hl.HL_TC_SPLIT)
         finally:
             hl.hl_destroy(h)
+    # 3D runs one shot
+    h = hl.hl_create_batch(3, 2, [[4, 4, 4], [5, 4, 4]], [0.2, 0.2])
+    try:
+        with pytest.raises(hl.HLError):
+            hl.hl_set_precision(h, hl.HL_TC_SPLIT)
+    finally:
+        hl.hl_destroy(h)
+
+
+# 3D (m = 2): the partner field cut once per half-step at the field's exponent, groups
+# of 4 vertices x 27 slots accumulated exactly on the tensor cores and drained into
+# float-float sums.  Grids: one tile ragged in x, several tiles with a ragged last one
+# (130 = 128 + 2), an exact tile multiple, and a cube with odd sizes per axis.
+@pytest.mark.parametrize("ncell,kind,steps", [([9, 7, 5], "random", 4), ([130, 3, 2], "random", 3),
+                                              ([128, 4, 3], "random", 3), ([16, 14, 12], "plane", 20),
+                                              ([2, 2, 2], "random", 5)])
+def test_tc_split_3d_error_against_oracle(ncell, kind, steps):
+    d, m = 3, 2
+    dt = I.cfl_dt(ncell)
+    st = I.plane_wave(m, ncell, dt, seed=3, kmax=2.0) if kind == "plane" else I.random_state(d, m, ncell, seed=140)
+    po, uo = oracle.run(d, m, ncell, dt, st.p, st.u, steps, prec="dd")
+    pg, ug = gpu_run(d, m, ncell, dt, st, steps, hl.HL_TC_SPLIT)
+    err = max(rel_err(pg, po), rel_err(ug, uo))
+    pf, uf = gpu_run(d, m, ncell, dt, st, steps, hl.HL_FP32)
+    err32 = max(rel_err(pf, po), rel_err(uf, uo))
+    print(f"tensor-core split error d=3 m=2 n={ncell} steps={steps}: {err:.2e} (FP32 {err32:.2e}, "
+          f"bound {tc_bound(d, m, steps):.2e})")
+    assert err <= tc_bound(d, m, steps)
+    assert err * 1e3 < err32
+
+
+def test_tc_split_3d_keeps_the_discretisation_error():
+    """3D plane wave, m = 2: the L2 error against the exact solution equals FP64's to 1%."""
+    d, m, ncell = 3, 2, [20, 20, 20]
+    dt = I.cfl_dt(ncell)
+    st = I.plane_wave(m, ncell, dt, seed=5, kmax=3.0)
+    steps = 40
+    ex = I.plane_wave(m, ncell, dt, seed=5, kmax=3.0, t0=steps * dt)
+    e = {}
+    for mode in (hl.HL_FP64, hl.HL_TC_SPLIT):
+        pg, _ = gpu_run(d, m, ncell, dt, st, steps, mode)
+        e[mode] = I.l2_error(d, ncell, pg, ex.p)
+    print("3D L2 error vs exact (FP64, TC_SPLIT):", e[hl.HL_FP64], e[hl.HL_TC_SPLIT])
+    assert abs(e[hl.HL_TC_SPLIT] - e[hl.HL_FP64]) <= 0.01 * e[hl.HL_FP64]
+
+
+def test_tc_split_3d_with_source_and_graph():
+    """A point source inside the tensor-core steps, launched plainly and from a graph."""
+    d, m, ncell = 3, 2, [12, 11, 10]
+    dt = I.cfl_dt(ncell)
+    st = I.random_state(d, m, ncell, seed=141)
+    src = dict(x0=[0.3, 0.6, 0.5], sigma=0.08, f0=6.0, amp=1.0)
+    steps = 4
+    po, uo = oracle.run_source(d, m, ncell, dt, st.p, st.u, steps, **src, prec="dd")
+    for graph in (0, 1):
+        h = hl.hl_create(d, m, ncell, dt)
+        try:
+            hl.hl_set_option(h, hl.HL_OPT_GRAPH, graph)
+            hl.hl_set_precision(h, hl.HL_TC_SPLIT)
+            hl.hl_set_initial(h, st.p, st.u)
+            hl.hl_set_source(h, src["x0"], src["sigma"], src["f0"], src["amp"])
+            hl.hl_step(h, steps)
+            pg, ug, _, _ = hl.hl_get_fields(h)
+        finally:
+            hl.hl_destroy(h)
+        assert max(rel_err(pg, po), rel_err(ug, uo)) <= tc_bound(d, m, steps), graph
 
 
 @pytest.mark.parametrize("mode", ["fp32_comp", "tc_split"])
