@@ -278,7 +278,7 @@ def test_tc_split_validation():
         finally:
             hl.hl_destroy(h)
     # 3D runs one shot
-    h = hl.hl_create_batch(3, 2, [[4, 4, 4], [5, 4, 4]], [0.2, 0.2])
+    h = hl.hl_create_batch(3, 2, [[4, 4, 4], [5, 4, 4]], [0.05, 0.05])
     try:
         with pytest.raises(hl.HLError):
             hl.hl_set_precision(h, hl.HL_TC_SPLIT)
