@@ -90,6 +90,41 @@ def dofs(dim=DIM, m=M, n=N):
     return (dim + 1) * (m + 1) ** dim * n ** dim
 
 
+def tc_issued_flops_per_step(dim, m, ncell):
+    """Dense FP16 tensor-core flops the split mode's MMAs issue in one leapfrog step: per
+    128-node tile and unit, data digit i multiplies 4 vertices' operands of K = 16 slots
+    by the 32-column (2D p-half: 16) blocks of levels i .. i + nlev_i - 1 (nlev = 7, 6, 5,
+    4, 3, 2: 27 level blocks)."""
+    if dim not in (2, 3):
+        return 0.0
+    tiles = -(-ncell[0] // 128) * int(math.prod(ncell[1:]))
+    lev_blocks = 27
+    per_block = 4 * 128 * 16 * 2                              # vertices x M x K x 2
+    if dim == 2:
+        units_cols = 2 * 16 + 1 * 32                           # p-half: 2 units of N 16; u-half: 1 of N 32
+    else:
+        units_cols = 12 * 32 + 12 * 32                         # 12 units a half, N 32 per level
+    return float(tiles * units_cols * lev_blocks * per_block)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def tc_roofline(dim, m, ncell, ms_per_step, peaks):
+    fl = tc_issued_flops_per_step(dim, m, ncell)
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    ach = fl / (ms_per_step / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "peak_source": ("measured bf16 sustained (FP16 has the same dense rate)" if peaks else "fallback"),
+            "flops": "dense FP16 MMA flops issued (digit pairs of 27 level blocks, padded slots included) over "
+                     "the whole step time (cut, exponent and tensor-core kernels)"}
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("hl_fp64.cuh",):  # the FP64 kernels' source
@@ -324,6 +359,8 @@ def run_aux(args, rank=0, world=1, dist=None):
             modes[name]["roofline"] = {"bound": "hbm", "achieved": modes[name]["hbm_gbs"], "peak": hbm,
                                        "unit": "GB/s", "frac": modes[name]["hbm_gbs"] / hbm,
                                        "peak_source": "measured" if peaks else "fallback"}
+            if name == "tc_split":
+                modes[name]["roofline"] = tc_roofline(d, m, ncell, modes[name]["ms_per_step"], peaks)
         if ex is not None:
             # equal L2 error: plain FP64 on coarser grids to the same final time; each
             # mode is compared with the coarsest FP64 grid whose error is no larger
@@ -978,6 +1015,8 @@ def run_headline(args):
                            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                         "frac": gbs / hbm, "peak_source": "measured" if peaks else "fallback",
                                         "bytes": "FP64 state read and written once per leapfrog step"}}
+            if name == "tc_split":
+                modes[name]["roofline"] = tc_roofline(DIM, M, ncell, ms / LF_STEPS, peaks)
         # equal L2 error: plain FP64 on coarser grids to the same final time; each mode is
         # set against the fastest FP64 grid whose error is no larger (equal within 1%)
         ladder = []
@@ -1090,6 +1129,8 @@ def run_modes_2d(hl, I, stream, n=512, m=3, lf=200, wave=(24, 24)):
         out[name] = {"value": dof / (ms / 1e3), "ms_per_run": ms, "l2_err_p_vs_exact": err, "status": rc,
                      "p_half_us": 1e3 * kt["p_half"] / max(kc["p_half"], 1),
                      "u_half_us": 1e3 * kt["u_half"] / max(kc["u_half"], 1)}
+        if name == "tc_split":
+            out[name]["roofline"] = tc_roofline(2, m, ncell, ms / lf, _peaks())
     t_end = lf * dt
     ladder = [{"n": n, "ms_run": out["fp64"]["ms_per_run"], "l2_err_p_vs_exact": out["fp64"]["l2_err_p_vs_exact"]}]
     for n2 in (192, 256, 320, 384, 448):

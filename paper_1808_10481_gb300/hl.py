@@ -21,6 +21,7 @@ HL_FP64 = 0
 HL_FP32 = 1
 HL_FP32_COMP = 2
 HL_TC_SPLIT = 3
+TC_SPLIT_DIMS = (2, 3)   # HL_TC_SPLIT: dim 2 (m <= 3), dim 3 (m = 2, one shot)
 HL_OPT_KERNEL_PATH = 1
 HL_OPT_TIMING = 2
 HL_OPT_GRAPH = 3
