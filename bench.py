@@ -55,7 +55,10 @@ FP64_PEAK_FLOPS = N_SM * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ * 1e9
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only while the kernel
 # source is unchanged (keyed by the hash of the kernel header); per workload.
 TRAFFIC_SOURCE_HASH = "5629d2e800a9a677"
-TRAFFIC_BYTES = {"2d": {"p_half": 103940096, "u_half": None}, "3d": {"p_half": None, "u_half": None}}
+# 3D: captured at 128^3 (2,097,152 nodes, 2.3 GB a launch, streaming) and scaled by the node
+# count to 256^3 (x8); the FP64 kernels read and write every node's data once per launch.
+TRAFFIC_BYTES = {"2d": {"p_half": 103940096, "u_half": None},
+                 "3d": {"p_half": 18202758144, "u_half": 25131762688}}
 
 WORKLOAD = ("3D acoustics p_t+div u=0, u_t+grad p=0, periodic unit cube, 256^3 nodes per grid, "
             "m=2 (27 scaled derivatives per node per field), FP64, plane wave with seeded wave vector "
