@@ -381,6 +381,32 @@ int hl_operator_table(int dim, int m, const double *lam, double *out);
  */
 #define HL_TC_TABLE_ELEMS 39168
 #define HL_TC_EXPO_ELEMS 48
+
+/*
+ * hl_tc_image -- the operator images the tensor-core split kernels load, as
+ * they load them (host only, no CUDA call), for inspection.  Entries are the
+ * FP16 bit patterns of the balanced base-256 digits of hl_tc_tables' scheme
+ * (integers in [-128, 127]); the entry is (sum_j digit_j 256^(5-j)) 2^(e - 46).
+ *   dim 2 (m <= 3): HL_TC_IMAGE2_ELEMS entries, p-half then u-half (14336
+ *     each): blocks b of [2 chunks][R rows][8 slots], slot l = chunk*8 + k;
+ *     p-half b = c*4 + v, R = 112, row n = j*16 + s; u-half b = v, R = 224,
+ *     row n = j*32 + i*16 + s (direction i); expo HL_TC_EXPO_ELEMS ints as in
+ *     hl_tc_tables.
+ *   dim 3 (m = 2): HL_TC_IMAGE3_ELEMS entries, p-half then u-half (172032
+ *     each): 12 units u = (i*2 + vz)*2 + kh (i: velocity component for the
+ *     p-half, direction for the u-half; vz the vertex's z bit; kh the half of
+ *     the 32 padded slots), each 4 vertex blocks vx + 2 vy of [2 chunks][224
+ *     rows n = j*32 + s][8 slots], slot l = kh*16 + chunk*8 + k; expo
+ *     HL_TC_EXPO3_ELEMS ints, e(op, s) at op*32 + s (op 0 the p-half, 1 + i
+ *     the u-half's direction i).
+ * Digit row block j = 6 and every slot beyond the node's (m+1)^dim are zero.
+ * lam[k] = dt/(2 h_k).  Returns HL_EINVAL for other (dim, m) or short buffers.
+ */
+#define HL_TC_IMAGE2_ELEMS 28672
+#define HL_TC_IMAGE3_ELEMS 344064
+#define HL_TC_EXPO3_ELEMS 128
+int hl_tc_image(int dim, int m, const double *lam, uint16_t *image, int64_t image_elems, int *expo,
+                int64_t expo_elems);
 int hl_tc_tables(int m, const double *lam, uint16_t *digits, int *expo);
 
 /*

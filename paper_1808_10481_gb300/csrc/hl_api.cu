@@ -320,8 +320,8 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         if (!build_tc3_images(h->m, h->coef.data(), img, ex))
             return set_err(h, HL_EINVAL, "3D tensor-core tables need m = 2");
         const Shot &sh = h->shots[0];
-        const size_t plane = (size_t)sh.n[1] * sh.n[2] * (sh.n[0] + 2);
-        const size_t ngu = 3 * 6 * 4 * plane + 256, ngp = 6 * 4 * plane + 256;
+        const size_t ngu = tc_plane_elems(3, 4, (int)sh.n[0], (int)sh.n[1], (int)sh.n[2]);
+        const size_t ngp = tc_plane_elems(1, 4, (int)sh.n[0], (int)sh.n[1], (int)sh.n[2]);
         HL_CK(h, cudaStreamSynchronize(h->stream));
         if (!h->tc_digits) HL_CK(h, cudaMalloc(&h->tc_digits, img.size() * sizeof(uint16_t)));
         if (!h->tc_expo) HL_CK(h, cudaMalloc(&h->tc_expo, ex.size() * sizeof(int)));
@@ -366,6 +366,17 @@ extern "C" int hl_set_precision(hl_solver *h, int mode)
         HL_CK(h, cudaMemcpy(h->tc_expo, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice));
         HL_CK(h, cudaMemcpy(h->tc_shots, sd.data(), sd.size() * sizeof(ShotDesc), cudaMemcpyHostToDevice));
         h->tc_tiles = (int)tiles;
+        if (h->shots.size() == 1) {
+            // one grid: digit planes of both fields, cut once per half-step (hl_tc2.cu)
+            const Shot &s0 = h->shots[0];
+            const size_t ngu = tc_plane_elems(2, 2, (int)s0.n[0], (int)s0.n[1], 1);
+            const size_t ngp = tc_plane_elems(1, 2, (int)s0.n[0], (int)s0.n[1], 1);
+            if (!h->tc3_emax) HL_CK(h, cudaMalloc(&h->tc3_emax, 2 * sizeof(int)));
+            if (!h->tc3_gu) HL_CK(h, cudaMalloc(&h->tc3_gu, ngu * sizeof(uint4)));
+            if (!h->tc3_gp) HL_CK(h, cudaMalloc(&h->tc3_gp, ngp * sizeof(uint4)));
+            HL_CK(h, cudaMemset(h->tc3_gu, 0, ngu * sizeof(uint4)));
+            HL_CK(h, cudaMemset(h->tc3_gp, 0, ngp * sizeof(uint4)));
+        }
     }
     h->precision = mode;
     return HL_OK;
@@ -601,7 +612,10 @@ static cudaError_t dispatch(int dim, const LaunchFp64 &a)
 {
     if (a.c2_primal) return dim == 1 ? launch_var_d1(a) : cudaErrorInvalidValue;
     if (a.split_coef && a.precision == HL_FP64) return launch_split(dim, a);
-    if (a.precision == HL_TC_SPLIT) return dim == 2 ? launch_tc_d2(a) : dim == 3 ? launch_tc_d3(a) : cudaErrorInvalidValue;
+    if (a.precision == HL_TC_SPLIT) {
+        if (dim == 2) return a.tc3_gu ? launch_tc2_planes(a) : launch_tc_d2(a);  // one grid : a batch
+        return dim == 3 ? launch_tc_d3(a) : cudaErrorInvalidValue;
+    }
     if (a.precision != HL_FP64) {
         switch (dim) {
         case 1: return launch_mixed_d1(a);
@@ -1002,6 +1016,29 @@ extern "C" int hl_tc_tables(int m, const double *lam, uint16_t *digits, int *exp
     std::vector<int> ex;
     if (!build_tc_tables(m, c.data(), dig, ex)) return set_err(nullptr, HL_EINVAL, "tensor-core tables need m <= 3");
     std::memcpy(digits, dig.data(), dig.size() * sizeof(uint16_t));
+    std::memcpy(expo, ex.data(), ex.size() * sizeof(int));
+    return HL_OK;
+}
+
+extern "C" int hl_tc_image(int dim, int m, const double *lam, uint16_t *image, int64_t image_elems, int *expo,
+                           int64_t expo_elems)
+{
+    static_assert(HL_TC_IMAGE2_ELEMS == kTc5ImageElems && HL_TC_IMAGE3_ELEMS == kTc3ImageElems,
+                  "tensor-core image sizes and header disagree");
+    if (!lam || !image || !expo || !((dim == 2 && m >= 0 && m <= 3) || (dim == 3 && m == 2)))
+        return set_err(nullptr, HL_EINVAL, "bad arguments (dim 2 with m <= 3, or dim 3 with m = 2)");
+    const int64_t need_img = dim == 2 ? HL_TC_IMAGE2_ELEMS : HL_TC_IMAGE3_ELEMS;
+    const int64_t need_ex = dim == 2 ? HL_TC_EXPO_ELEMS : HL_TC_EXPO3_ELEMS;
+    if (image_elems < need_img || expo_elems < need_ex) return set_err(nullptr, HL_EINVAL, "buffers too short");
+    const double l3[3] = {lam[0], lam[1], dim == 3 ? lam[2] : 0.0};
+    std::vector<double> c;
+    if (!build_operator(dim, m, l3, c)) return set_err(nullptr, HL_EINVAL, "operator construction failed");
+    std::vector<uint16_t> img;
+    std::vector<int> ex;
+    const bool ok = dim == 2 ? build_tc5_images(m, c.data(), img, ex) : build_tc3_images(m, c.data(), img, ex);
+    if (!ok || (int64_t)img.size() != need_img || (int64_t)ex.size() != need_ex)
+        return set_err(nullptr, HL_EINVAL, "tensor-core image construction failed");
+    std::memcpy(image, img.data(), img.size() * sizeof(uint16_t));
     std::memcpy(expo, ex.data(), ex.size() * sizeof(int));
     return HL_OK;
 }

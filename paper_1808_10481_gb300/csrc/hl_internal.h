@@ -129,6 +129,12 @@ cudaError_t launch_mixed_d2(const LaunchFp64 &a);
 cudaError_t launch_mixed_d3(const LaunchFp64 &a);
 cudaError_t launch_tc_d2(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m <= 3
 cudaError_t launch_tc_d3(const LaunchFp64 &a);     // precision HL_TC_SPLIT, m = 2, one shot
+cudaError_t launch_tc2_planes(const LaunchFp64 &a);  // HL_TC_SPLIT, dim = 2, one shot, digit planes
+// elements (uint4) of a field's digit planes (hl_tc_planes.cuh)
+inline size_t tc_plane_elems(int ncomp, int CH, int n0, int n1, int n2)
+{
+    return (size_t)ncomp * 6 * CH * (size_t)n1 * n2 * (size_t)(n0 + 2) + 256;
+}
 cudaError_t launch_var_d1(const LaunchFp64 &a);    // variable wave speed, dim = 1, FP64
 cudaError_t launch_split(int dim, const LaunchFp64 &a);  // split two-kernel FP64 ablation, m <= 3
 // ghost planes of the walled axes (kinds: 0 periodic, 1 dirichlet, 2 neumann), in axis order

@@ -12,10 +12,11 @@
 //     with the data, by bulk copy.
 //   * Cutting the partner data into digits inside the tile (as in 2D) would cut
 //     every value 4 times (each node is a vertex of 4 tiles' cells along y and z);
-//     instead one pass (k_tc3_cut) cuts every partner value once per half-step into
+//     instead one pass (k_tc_cut) cuts every partner value once per half-step into
 //     digit planes in global memory, at one exponent per field (the field's
-//     largest binary exponent, k_tc3_emax), and the tensor-core kernel only copies
-//     digit rows into shared memory.
+//     largest binary exponent: k_tc_emax at the first step of a call, afterwards
+//     the maximum the kernel that wrote the field took over its outputs), and the
+//     tensor-core kernel only copies digit rows into shared memory.
 //
 // Digit planes of a field with C components: entry (c, i, ch, r, xe) is 16 bytes
 // = 8 FP16 digits i of slots 8 ch .. 8 ch + 7 of component c at node row
@@ -45,6 +46,7 @@
 #include "hl_sm100.cuh"
 #include "hl_split.cuh"
 #include "hl_tc5.cuh"
+#include "hl_tc_planes.cuh"
 
 namespace hl {
 
@@ -61,6 +63,7 @@ constexpr int kStages = 2;
 constexpr int kTxBytes = 24 * kRowBytes + kBBytes;
 constexpr int kThreads = 320;              // producer, MMA, 8 epilogue warps
 constexpr int kEpiWarp0 = 2;
+static_assert(kThreads == 32 * (kEpiWarp0 + 8), "role layout: every warp after the MMA warp is an epilogue warp");
 constexpr int kAccCols = 7 * 32;           // one accumulator: 7 levels x 32 columns
 constexpr int kSmemBytes = kStages * kStageBytes + 8 * (4 * kStages + 1) + 16;
 static_assert(kTxBytes < (1 << 20), "transaction count");
@@ -85,67 +88,13 @@ __device__ __forceinline__ void mbar_arrive1(uint32_t mbar)
 
 }  // namespace
 
-// Largest biased binary exponent of a field (all components and slots) into
-// *emax (which the caller zeroes first).  Non-finite values set status bit 1
-// and are left out.
-__global__ void __launch_bounds__(256) k_tc3_emax(const double *__restrict__ F, int64_t n, int *emax,
-                                                  unsigned *status)
-{
-    int e = 0;
-    bool bad = false;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int ek = (__double2hiint(__ldg(F + k)) >> 20) & 0x7FF;
-        bad |= ek == 0x7FF;
-        e = max(e, ek == 0x7FF ? 0 : ek);
-    }
-    report_nonfinite(bad, status);
-    e = __reduce_max_sync(0xFFFFFFFFu, e);
-    if ((threadIdx.x & 31) == 0) atomicMax(emax, e);
-}
-
-// Cut every value of a field into its digit planes (layout above), at the
-// field's exponent *emax: one thread per (component, row, xe); grid (xe blocks,
-// n1, n2 * ncomp).
-__global__ void __launch_bounds__(128) k_tc3_cut(const double *__restrict__ F, uint4 *__restrict__ G, int ncomp,
-                                                 int n0, int n1, int n2, const int *__restrict__ emaxp)
-{
-    const int xe = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.z / n2;
-    const int r = blockIdx.y + n1 * (blockIdx.z % n2);
-    if (xe >= n0 + 2 || c >= ncomp) return;
-    int x = xe - 1;
-    if (x < 0) x += n0;
-    if (x >= n0) x -= n0;
-    const int64_t nnode = (int64_t)n0 * n1 * n2;
-    const int64_t node = x + (int64_t)n0 * r;
-    const int emax = __ldg(emaxp);
-    const int64_t R = (int64_t)n1 * n2, XE = n0 + 2;
-    const double *src = F + (int64_t)c * kNQ * nnode + node;
-#pragma unroll
-    for (int ch = 0; ch < kChunks; ++ch) {
-        int64_t y[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int s = ch * 8 + k;
-            y[k] = t5_fixed(s < kNQ ? __ldg(src + (int64_t)s * nnode) : 0.0, emax);
-        }
-        uint32_t w[4][kT5Digits];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t5_digits_f16x2(y[2 * k], y[2 * k + 1], w[k]);
-#pragma unroll
-        for (int i = 0; i < kT5Digits; ++i)
-            G[(((int64_t)(c * kT5Digits + i) * kChunks + ch) * R + r) * XE + xe] =
-                make_uint4(w[0][i], w[1][i], w[2][i], w[3][i]);
-    }
-}
-
 // One half-step on the tensor cores.  PHALF: X = p, partner digits of u (3
 // components), operator 0; else X = u (3 directions), partner digits of p.
 template <bool PHALF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_half_tc3(const uint4 *__restrict__ G, double *__restrict__ X, int n0, int n1, int n2, int total_tiles,
                const uint4 *__restrict__ Bimg, const int *__restrict__ expo, const int *__restrict__ emaxp,
-               unsigned *status)
+               int *emax_out, unsigned *status)
 {
     extern __shared__ __align__(1024) unsigned char t3_sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(t3_sm + kStages * kStageBytes);
@@ -291,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
         constexpr int GPS = PHALF ? 6 : 2;             // groups per output set
         const int E = __ldg(emaxp) - 1022;
-        int gg = 0;
+        int gg = 0, emx = 0;  // emx: largest biased exponent written (the next cut's field exponent)
         bool bad = false;
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             if (*abort_flag) break;
@@ -373,13 +322,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const double inc = t5_scaled_f64(nrm.hi, k0) + t5_scaled_f64(nrm.lo, k0);
                             const double nv = own[cg][j] + inc;
                             X[(int64_t)(os * kNQ + s) * nnode + node] = nv;
-                            bad |= nonfinite(nv);
+                            const int ev = (__double2hiint(nv) >> 20) & 0x7FF;
+                            bad |= ev == 0x7FF;
+                            emx = max(emx, ev == 0x7FF ? 0 : ev);
                         }
                 }
             }
             if (quit) break;
         }
         report_nonfinite(bad, status);
+        emx = __reduce_max_sync(0xFFFFFFFFu, emx);
+        if (lane == 0) atomicMax(emax_out, emx);
     }
     tc_fence_before();
     __syncthreads();
@@ -414,23 +367,32 @@ cudaError_t launch_tc_d3(const LaunchFp64 &a)
     const uint4 *bu = reinterpret_cast<const uint4 *>(a.tc_digits + kTc3ImageElems / 2);
     const unsigned red_blocks = (unsigned)std::min<int64_t>((nnode * 3 * kNQ + 255) / 256, 8 * sms);
     int *emax_u = a.tc3_emax, *emax_p = a.tc3_emax + 1;
+    // Field exponents: each tensor-core kernel takes the largest exponent of the values it
+    // writes (atomic maximum over its warps), which the next half-step's cut of that field
+    // uses; only the first step of a call (the state may have been set or changed since) and
+    // a point source (it adds to p after the p-half) need the separate pass.
+    const bool src = a.src && a.src->active;
     for (int64_t st = 0; st < a.nsteps; ++st) {
         if (a.ev) cudaEventRecord(a.ev[2 * st], a.stream);
-        // p-half: the velocity's exponent and digit planes, then the products
-        if ((e = cudaMemsetAsync(emax_u, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
-        k_tc3_emax<<<red_blocks, 256, 0, a.stream>>>(a.U, nnode * 3 * kNQ, emax_u, a.status);
-        k_tc3_cut<<<dim3(cut_x, (unsigned)n1, (unsigned)(3 * n2)), 128, 0, a.stream>>>(a.U, a.tc3_gu, 3, n0, n1, n2, emax_u);
+        // p-half: the velocity's digit planes, then the products
+        if (st == 0) {
+            if ((e = cudaMemsetAsync(emax_u, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
+            k_tc_emax<0><<<red_blocks, 256, 0, a.stream>>>(a.U, nnode * 3 * kNQ, emax_u, a.status);
+        }
+        k_tc_cut<kNQ, kChunks><<<dim3(cut_x, (unsigned)n1, (unsigned)(3 * n2)), 128, 0, a.stream>>>(a.U, a.tc3_gu, 3, n0, n1, n2, emax_u);
+        if ((e = cudaMemsetAsync(emax_p, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
         k_half_tc3<true><<<grid, kThreads, kSmemBytes, a.stream>>>(a.tc3_gu, a.P, n0, n1, n2, tiles, bp, a.tc_expo,
-                                                                   emax_u, a.status);
-        if (a.src && a.src->active) {
+                                                                   emax_u, emax_p, a.status);
+        if (src) {
             if ((e = launch_source(*a.src, a.shots, a.P, kNQ, a.step0 + st, a.stream)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(emax_p, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
+            k_tc_emax<0><<<red_blocks, 256, 0, a.stream>>>(a.P, nnode * kNQ, emax_p, a.status);
         }
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
-        if ((e = cudaMemsetAsync(emax_p, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
-        k_tc3_emax<<<red_blocks, 256, 0, a.stream>>>(a.P, nnode * kNQ, emax_p, a.status);
-        k_tc3_cut<<<dim3(cut_x, (unsigned)n1, (unsigned)n2), 128, 0, a.stream>>>(a.P, a.tc3_gp, 1, n0, n1, n2, emax_p);
+        k_tc_cut<kNQ, kChunks><<<dim3(cut_x, (unsigned)n1, (unsigned)n2), 128, 0, a.stream>>>(a.P, a.tc3_gp, 1, n0, n1, n2, emax_p);
+        if ((e = cudaMemsetAsync(emax_u, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
         k_half_tc3<false><<<grid, kThreads, kSmemBytes, a.stream>>>(a.tc3_gp, a.U, n0, n1, n2, tiles, bu, a.tc_expo,
-                                                                    emax_p, a.status);
+                                                                    emax_p, emax_u, a.status);
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
     return cudaGetLastError();

@@ -32,6 +32,7 @@ HL_WALL_PERIODIC, HL_WALL_DIRICHLET, HL_WALL_NEUMANN = 0, 1, 2
 HL_NUM_TILES = 14
 HL_NOALLOC_SCRATCH_BYTES = 65536
 HL_TC_TABLE_ELEMS, HL_TC_EXPO_ELEMS = 39168, 48
+HL_TC_IMAGE2_ELEMS, HL_TC_IMAGE3_ELEMS, HL_TC_EXPO3_ELEMS = 28672, 344064, 128
 HL_MLP_IN, HL_MLP_HIDDEN, HL_MLP_OUT, HL_MLP_NPARAMS = 288, 128, 16, 55568
 TILES = [(128, 1), (256, 1), (64, 2), (32, 4), (32, 8), (64, 4), (16, 8), (16, 16),
          (32, 4, "paired"), (32, 8, "paired"), (64, 4, "paired"), (16, 16, "paired"),
@@ -79,6 +80,7 @@ _SIGNATURES = [
     ("hl_kernel_times", ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     ("hl_operator_table", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("hl_tc_tables", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), _P, _P]),
+    ("hl_tc_image", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D), _P, _I64, _P, _I64]),
     ("hl_mlp_create", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(_P)]),
     ("hl_mlp_destroy", None, [_P]),
     ("hl_mlp_last_error", ctypes.c_char_p, [_P]),
@@ -370,6 +372,23 @@ def hl_tc_tables(m: int, lam):
     if rc != HL_OK:
         raise HLError(rc, hl_last_error(None))
     return digits.reshape(3, 6, 16, 136), expo.reshape(3, 16)
+
+
+def hl_tc_image(dim: int, m: int, lam):
+    """The tensor-core kernels' operator images (FP16 bit patterns, uint16) and column
+    exponents: dim 2 -> ((2, 14336), (3, 16)); dim 3 -> ((2, 12, 4, 2, 224, 8), (4, 32))."""
+    n_img = HL_TC_IMAGE2_ELEMS if dim == 2 else HL_TC_IMAGE3_ELEMS
+    n_ex = HL_TC_EXPO_ELEMS if dim == 2 else HL_TC_EXPO3_ELEMS
+    image = np.zeros(n_img, dtype=np.uint16)
+    expo = np.zeros(n_ex, dtype=np.int32)
+    lm = (_D * 3)(*([float(x) for x in lam[:3]] + [0.0] * (3 - len(lam[:3]))))
+    rc = load().hl_tc_image(int(dim), int(m), lm, ctypes.c_void_p(image.ctypes.data), n_img,
+                            ctypes.c_void_p(expo.ctypes.data), n_ex)
+    if rc != HL_OK:
+        raise HLError(rc, hl_last_error(None))
+    if dim == 2:
+        return image.reshape(2, 14336), expo.reshape(3, 16)
+    return image.reshape(2, 12, 4, 2, 224, 8), expo.reshape(4, 32)
 
 
 def hl_step_noalloc(dim: int, m: int, n_cells, dt: float, p_dev, u_dev, n_steps: int, stream=None) -> int:
