@@ -90,13 +90,14 @@ enum {
                             the fifth-generation tensor cores (tcgen05.mma,
                             FP32 accumulators in tensor memory): the binary64
                             partner data (scaled by the largest power of two
-                            of a 128-node tile's region in 2D, of the whole
-                            field in 3D) and the operator cut into 6
+                            of the whole field, or of a 128-node tile's
+                            region for a batch of 2D shots) and the
+                            operator cut into 6
                             base-256 digits; the digit pairs of the 7
                             leading levels are summed, each level exactly,
                             then in float-float; about 46 bits below that
-                            maximum.  3D allocates digit planes of both
-                            fields (1.5x the state's size)                  */
+                            maximum.  One grid allocates digit planes of
+                            both fields (1.5x the state's size)             */
 };
 
 /*
