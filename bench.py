@@ -407,7 +407,7 @@ def run_aux(args, rank=0, world=1, dist=None):
                     "config": {"workload": desc, "dim": d, "m": m, "n_cells": ncell, "leapfrog_steps": lf},
                     "modes": modes})
     elif args.workload == "learned":
-        out.update(run_learned(args, n_train=args.train_seeds, n_test=args.test_seeds))
+        out.update(run_learned(args, n_train=args.train_seeds, n_test=args.test_seeds, dist=dist))
     elif args.workload == "split3d":
         out.update(run_split3d(hl, I, stream))
     elif args.workload in ("modified1d", "variable1d"):
@@ -597,14 +597,21 @@ def run_1d_variant(workload, hl, I, stream):
             "config": {"workload": desc, "dim": 1, "m": m, "n_cells": [n]}}
 
 
-def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
+def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000, dist=None):
     """Learned coarse-grid correction at the workload's scale: coarse 256^2 vs fine 1024^2,
-    m = 3, seeded Gaussian pulses and Ricker sources; the fine FP64 solver is the reference."""
+    m = 3, seeded Gaussian pulses and Ricker sources; the fine FP64 solver is the reference.
+    Under torchrun the training seeds are sharded over the ranks and the network trains data-
+    parallel (gradients averaged by all-reduce before every Adam step); rank 0 evaluates."""
     import numpy as np
     import torch
 
     from paper_1808_10481_gb300 import hl
     from paper_1808_10481_gb300 import inputs as I
+    from paper_1808_10481_gb300 import learned
+
+    world = dist.get_world_size() if dist is not None else 1
+    rank = dist.get_rank() if dist is not None else 0
+    train_lo, train_hi = learned.shard_range(n_train, world, rank)
 
     nc, r = [256, 256], 4
     nf = [nc[0] * r, nc[1] * r]
@@ -639,41 +646,44 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
         torch.cuda.synchronize()
         return hc, hf, t0.elapsed_time(t1), t1.elapsed_time(t2)
 
-    gen_rng = np.random.default_rng(0)
     per_seed = 16384
-    n = n_train * per_seed
+    n = (train_hi - train_lo) * per_seed
     X = torch.empty((n, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
     T = torch.empty((n, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
     t_coarse = t_fine = 0.0
     wall = time.perf_counter()
-    for i in range(n_train):
+    for k, i in enumerate(range(train_lo, train_hi)):
+        gen_rng = np.random.default_rng(10_000 + i)    # the training nodes of seed i
         hc, hf, tc, tf = pair(seed0 + i)
         t_coarse += tc
         t_fine += tf
         nodes = torch.from_numpy(gen_rng.choice(rows, per_seed, replace=False).astype(np.int32)).to(dev)
-        hl.hl_features(hc, nodes, per_seed, 1.0, 0.0, X[i * per_seed:(i + 1) * per_seed])
-        hl.hl_targets(hf, r, hc, nodes, per_seed, 1.0, T[i * per_seed:(i + 1) * per_seed])
+        hl.hl_features(hc, nodes, per_seed, 1.0, 0.0, X[k * per_seed:(k + 1) * per_seed])
+        hl.hl_targets(hf, r, hc, nodes, per_seed, 1.0, T[k * per_seed:(k + 1) * per_seed])
         hl.hl_destroy(hc)
         hl.hl_destroy(hf)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - wall
-    out_scale = float(T.pow(2).mean().sqrt())
+    # one output scale for every rank: the RMS of all training targets
+    ss = torch.tensor([float(T.pow(2).sum()), float(T.numel())], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ss)
+    out_scale = float((ss[0] / ss[1]).sqrt())
     T /= out_scale
     net = hl.hl_mlp_create(7)
     hl.hl_mlp_set_stream(net, stream)
     iters, batch = 3000, 8192
-    Xb = torch.empty((batch, hl.HL_MLP_IN), dtype=torch.float32, device=dev)
-    Tb = torch.empty((batch, hl.HL_MLP_OUT), dtype=torch.float32, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for it in range(iters):   # stream-ordered: draw, loss and gradient, Adam; no host round trip
-        hl.hl_mlp_sample(net, X, T, batch, 0, it, Xb, Tb)
-        hl.hl_mlp_loss_grad(net, Xb, Tb, batch, want_loss=False)
-        hl.hl_mlp_adam_step(net, 1e-3 if it < 2000 else 2e-4)
+    # stream-ordered: draw, loss and gradient, gradient all-reduce (several ranks), Adam
+    learned.train(net, X, T, iters, batch, lambda it: 1e-3 if it < 2000 else 2e-4, seed=0, dist=dist)
     e1.record(stream)
     final_loss = hl.hl_mlp_loss_grad(net, X[:65536].contiguous(), T[:65536].contiguous(), min(n, 65536))
     train_ms = e0.elapsed_time(e1)
     del X, T
+    if rank != 0:
+        hl.hl_mlp_destroy(net)
+        return {}
     # held-out seeds, one pair at a time: plain error, correction, corrected error
     plain = corr = 0.0
     plain0 = corr0 = 0.0
@@ -698,7 +708,7 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
         hl.hl_destroy(hc)
         hl.hl_destroy(hf)
     hl.hl_mlp_destroy(net)
-    n_seeds = n_train + n_test
+    n_seeds = (train_hi - train_lo) + n_test   # the pairs this rank ran and timed
     dof_c = 3 * 16 * rows * horizon
     dof_f = 3 * 16 * rows * r * r * horizon * r
     return {
@@ -708,7 +718,8 @@ def run_learned(args, n_train=96, n_test=32, horizon=32, seed0=1000):
                                f"{n_train} training + {n_test} held-out seeds (Gaussian pulses width U[0.012,0.025] "
                                f"and Ricker sources f0 U[10,20]), horizon {horizon} coarse steps",
                    "mlp": "288-128-128-16, BF16 tensor-core products, FP32 accumulate, Adam",
-                   "train_iters": iters, "batch": batch, "train_rows": n},
+                   "train_iters": iters, "batch_per_rank": batch, "train_rows": n_train * per_seed,
+                   "data_parallel_ranks": world},
         "held_out_rms_err_plain": (plain / (n_test * rows * 16)) ** 0.5,
         "held_out_rms_err_corrected": (corr / (n_test * rows * 16)) ** 0.5,
         "gain_all_slots": (plain / corr) ** 0.5,
@@ -1170,7 +1181,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.workload == "batch" or rank == 0:
+    if args.workload in ("batch", "learned") or rank == 0:
         run_aux(args, rank, world, dist)
     if dist:
         dist.destroy_process_group()

@@ -558,6 +558,18 @@ int hl_mlp_sample(hl_mlp *mlp, const float *X_pool, const float *T_pool, int64_t
 int hl_mlp_adam_step(hl_mlp *mlp, float lr);
 
 /*
+ * hl_mlp_grad_buffer -- *grads_dev receives the device address of the
+ * network's gradient: HL_MLP_NPARAMS floats (the parameter layout of
+ * hl_mlp_params), owned by the network and valid until hl_mlp_destroy, written
+ * by hl_mlp_loss_grad (the gradient of the mean squared error over its rows)
+ * and read by hl_mlp_adam_step, both on the network's stream.  Data-parallel
+ * training reduces it in place between those two calls, on that stream: with
+ * equal rows per rank, the mean over the ranks is the gradient of the mean loss
+ * over all their rows.  No CUDA call; HL_EINVAL for NULL arguments.
+ */
+int hl_mlp_grad_buffer(hl_mlp *mlp, float **grads_dev);
+
+/*
  * hl_features -- X_dev[rows][288] for the coarse primal nodes nodes_dev[rows]
  * (device int array; NULL = nodes 0..rows-1) of a single 2D m = 3 grid, on the
  * solver's stream.  Nodes outside the grid give zero rows.

@@ -655,6 +655,15 @@ extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_de
     return HL_OK;
 }
 
+extern "C" int hl_mlp_grad_buffer(hl_mlp *h, float **grads_dev)
+{
+    if (!grads_dev) return mlp_err(h, HL_EINVAL, "grads_dev is NULL");
+    int rc = mlp_check(h);
+    if (rc) return rc;
+    *grads_dev = h->g;
+    return HL_OK;
+}
+
 extern "C" int hl_mlp_adam_step(hl_mlp *h, float lr)
 {
     int rc = mlp_check(h);

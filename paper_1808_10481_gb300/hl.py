@@ -89,6 +89,7 @@ _SIGNATURES = [
     ("hl_mlp_forward", ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     ("hl_mlp_loss_grad", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(_D)]),
     ("hl_mlp_adam_step", ctypes.c_int, [_P, ctypes.c_float]),
+    ("hl_mlp_grad_buffer", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p)]),
     ("hl_mlp_sample", ctypes.c_int, [_P, _P, _P, _I64, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _P, _P]),
     ("hl_features", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
     ("hl_targets", ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _D, _P]),
@@ -508,6 +509,29 @@ def hl_mlp_loss_grad(m: MLP, X, T, rows: int, want_loss: bool = True):
 
 def hl_mlp_adam_step(m: MLP, lr: float) -> None:
     _mcheck(m, load().hl_mlp_adam_step(m.ptr, ctypes.c_float(lr)))
+
+
+class _DeviceFloats:
+    """A device float array exposed through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def hl_mlp_grad_buffer(m: MLP) -> int:
+    """Device address of the network's gradient (HL_MLP_NPARAMS floats, owned by the network)."""
+    ptr = ctypes.c_void_p()
+    _mcheck(m, load().hl_mlp_grad_buffer(m.ptr, ctypes.byref(ptr)))
+    return int(ptr.value)
+
+
+def hl_mlp_grad_tensor(m: MLP):
+    """The network's gradient buffer as a torch tensor sharing its device memory
+    (HL_MLP_NPARAMS floats; valid while the network lives): data-parallel training
+    reduces it in place between hl_mlp_loss_grad and hl_mlp_adam_step."""
+    import torch
+    return torch.as_tensor(_DeviceFloats(hl_mlp_grad_buffer(m), HL_MLP_NPARAMS), device="cuda")
 
 
 def hl_mlp_sample(m: MLP, X_pool, T_pool, rows: int, seed: int, step: int, X, T=None) -> None:

@@ -205,6 +205,54 @@ def test_adam_step_matches_oracle_elementwise(net):
             assert np.all(np.abs(Gw[k] - w[k]) <= tol), (k, t, float(np.abs(Gw[k] - w[k]).max()))
 
 
+def test_grad_buffer_is_the_gradient_adam_reads():
+    """hl_mlp_grad_tensor shares the network's gradient: it equals the host copy after
+    hl_mlp_loss_grad, and an in-place change (as a data-parallel all-reduce makes) is what
+    the next Adam step uses: zeroed, the first step leaves every weight unchanged."""
+    m = hl.hl_mlp_create(77)
+    try:
+        rows = 128
+        X, T = _batch(rows, 21)
+        hl.hl_mlp_loss_grad(m, torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV), rows, want_loss=False)
+        g = hl.hl_mlp_grad_tensor(m)
+        torch.cuda.synchronize()
+        w0, g_host = hl.hl_mlp_params(m, want_grads=True)
+        assert g.shape == (hl.HL_MLP_NPARAMS,) and np.array_equal(g.cpu().numpy(), g_host)
+        g.zero_()
+        hl.hl_mlp_adam_step(m, 1e-3)
+        w1, g2 = hl.hl_mlp_params(m, want_grads=True)
+        assert not g2.any() and np.array_equal(w0, w1)
+    finally:
+        hl.hl_mlp_destroy(m)
+
+
+def test_data_parallel_train_on_one_rank_is_the_plain_loop():
+    """learned.train on a single rank (no all-reduce) equals the draw / loss-and-gradient /
+    Adam loop bitwise."""
+    from paper_1808_10481_gb300 import learned
+    rows, batch, iters = 4096, 256, 5
+    X, T = _batch(rows, 22)
+    Xd, Td = torch.from_numpy(X).to(DEV), torch.from_numpy(T).to(DEV)
+    a, b = hl.hl_mlp_create(5), hl.hl_mlp_create(5)
+    try:
+        st = torch.cuda.current_stream()
+        hl.hl_mlp_set_stream(a, st)
+        hl.hl_mlp_set_stream(b, st)
+        learned.train(a, Xd, Td, iters, batch, lambda it: 1e-3, seed=3)
+        Xb = torch.empty((batch, hl.HL_MLP_IN), dtype=torch.float32, device=DEV)
+        Tb = torch.empty((batch, hl.HL_MLP_OUT), dtype=torch.float32, device=DEV)
+        for it in range(iters):
+            hl.hl_mlp_sample(b, Xd, Td, batch, 3, it, Xb, Tb)
+            hl.hl_mlp_loss_grad(b, Xb, Tb, batch, want_loss=False)
+            hl.hl_mlp_adam_step(b, 1e-3)
+        wa, _ = hl.hl_mlp_params(a)
+        wb, _ = hl.hl_mlp_params(b)
+        assert np.array_equal(wa, wb)
+    finally:
+        hl.hl_mlp_destroy(a)
+        hl.hl_mlp_destroy(b)
+
+
 def test_adam_training_fits_a_smooth_map(net):
     """The kernels learn: a fixed random smooth map is fitted to a fraction of its variance."""
     rows = 4096
