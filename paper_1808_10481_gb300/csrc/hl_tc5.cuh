@@ -47,6 +47,7 @@
 #include "hl_fp64.cuh"
 #include "hl_sm100.cuh"
 #include "hl_split.cuh"
+#include "hl_tc_bits.cuh"
 
 namespace hl {
 
@@ -54,7 +55,6 @@ constexpr int kT5TileX = 128;                 // nodes per tile (MMA rows)
 constexpr int kT5RX = kT5TileX + 1;           // region nodes per grid row
 constexpr int kT5Rows = 2 * kT5RX;            // region nodes (two grid rows)
 constexpr int kT5RowsPad = 264;               // rows of a digit plane (multiple of 8)
-constexpr int kT5Digits = 6;
 constexpr int kT5Levels = 7;
 constexpr int kT5Chunk = kT5RowsPad * 16;     // bytes of one 8-slot plane: 264 rows of 16 B
 constexpr int kT5Plane = 2 * kT5Chunk;        // one digit of one component (16 slots)
@@ -75,25 +75,6 @@ struct T5Op {
     static_assert((PHALF ? 8 : 4) * KB_BYTES == kT5BBytes, "operator image size");
 };
 
-// Fixed-point form of one binary64 value at the block exponent, with every byte
-// below the top digit biased by 128 (emax is the largest biased exponent of the
-// region, |v| < 2^(emax - 1022) = 2^E):  X = trunc(v 2^(48 - E)), |X| < 2^48,
-// returned as y = X + 0x8080808080, so that byte k of y (k < 5) is d_(5-k) + 128
-// and y >> 40 (arithmetic) is d_0 in [-256, 256].  Integer operations only.
-__device__ __forceinline__ int64_t t5_fixed(double v, int emax)
-{
-    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const int sh = emax + 5 - e;  // >= 5 whenever e <= emax
-    uint64_t mag = 0;
-    if (e != 0 && e != 0x7FF && sh < 64) {
-        const uint64_t m53 = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-        mag = m53 >> sh;
-    }
-    const int64_t x = (hi >> 31) ? -(int64_t)mag : (int64_t)mag;
-    return x + 0x8080808080ll;
-}
-
 // The six digits of two biased fixed-point values a and b (adjacent slots) as
 // FP16 pairs, w[i] = (digit i of a, digit i of b), low half first.  Digits 1..5
 // are the biased bytes 4..0: one byte permutation puts each under the exponent
@@ -109,32 +90,10 @@ __device__ __forceinline__ uint32_t t5_sub_f16x2(uint32_t x, uint32_t c)
 
 __device__ __forceinline__ void t5_digits_f16x2(int64_t a, int64_t b, uint32_t (&w)[kT5Digits])
 {
-    constexpr uint32_t kHi = 0x64646464u;
-    const uint32_t alo = (uint32_t)a, blo = (uint32_t)b;
-    const uint32_t ahi = (uint32_t)((uint64_t)a >> 32), bhi = (uint32_t)((uint64_t)b >> 32);
-    const uint32_t P = __byte_perm(alo, blo, 0x5140);   // a.b0 b.b0 a.b1 b.b1
-    const uint32_t Q = __byte_perm(alo, blo, 0x7362);   // a.b2 b.b2 a.b3 b.b3
-    const uint32_t R = __byte_perm(ahi, bhi, 0x4040);   // a.b4 b.b4 (twice)
-    w[5] = t5_sub_f16x2(__byte_perm(P, kHi, 0x4140), 0x64806480u);
-    w[4] = t5_sub_f16x2(__byte_perm(P, kHi, 0x4342), 0x64806480u);
-    w[3] = t5_sub_f16x2(__byte_perm(Q, kHi, 0x4140), 0x64806480u);
-    w[2] = t5_sub_f16x2(__byte_perm(Q, kHi, 0x4342), 0x64806480u);
-    w[1] = t5_sub_f16x2(__byte_perm(R, kHi, 0x4140), 0x64806480u);
-    const uint32_t ta = (uint32_t)(((int)ahi >> 8) + (512 + 0x6400));
-    const uint32_t tb = (uint32_t)(((int)bhi >> 8) + (512 + 0x6400));
-    w[0] = t5_sub_f16x2(__byte_perm(ta, tb, 0x5410), 0x66006600u);
-}
-
-// exact f * 2^k as binary64 (f normal or zero; integer operations only)
-__device__ __forceinline__ double t5_scaled_f64(float f, int k)
-{
-    const uint32_t b = __float_as_uint(f);
-    if ((b & 0x7FFFFFFFu) == 0u) return 0.0;
-    const int eh = (int)((b >> 23) & 0xFFu) + 896 + k;
-    if (eh <= 0) return 0.0;
-    const uint32_t m = b & 0x7FFFFFu;
-    if (eh >= 2047) return __hiloint2double((int)((b & 0x80000000u) | 0x7FF00000u), 0);
-    return __hiloint2double((int)((b & 0x80000000u) | ((uint32_t)eh << 20) | (m >> 3)), (int)(m << 29));
+    t5_digit_words(a, b, w);
+#pragma unroll
+    for (int i = 1; i < kT5Digits; ++i) w[i] = t5_sub_f16x2(w[i], kT5SubLow);
+    w[0] = t5_sub_f16x2(w[0], kT5SubTop);
 }
 
 // the 6 digit-plane entries (16 bytes each) of one 8-slot chunk of one region row
