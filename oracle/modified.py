@@ -26,7 +26,7 @@ experiment that follows them):
     and the sums run over every term with s + k <= 2m + 1 (the full series: beyond that
     degree the interpolants' derivatives vanish).
 
-Readings of the garbled printed formulas (recorded in the design doc): eq. lfw2 prints the space
+Readings of the garbled printed formulas: eq. lfw2 prints the space
 derivative of order l inside the sum where order i is meant, and its limits 2+l..2m-1 are
 read as the full series k = 0, 2, 4, ... with l + k <= 2m + 1 (the k = 0 term is the 2 f~_s
 of the midpoint value, without which the sum of the two expansions is not consistent).

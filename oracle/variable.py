@@ -23,7 +23,7 @@ for the variable coefficient):
      the u-half (the interpolant is P_0 = p at the midpoint), keeping slots 0..m.
 The time series stops at order 2m+1, the interpolant's degree: with constant c it is the
 full series of the constant-coefficient scheme (the terms beyond vanish there).  Readings
-(recorded in the design doc): the printed c~_i = h!/i! ... is read as h^i/i!; polynomials in the
+of the garbled formulas: the printed c~_i = h!/i! ... is read as h^i/i!; polynomials in the
 recurrence are kept to degree 2m+1.
 """
 from __future__ import annotations

@@ -64,7 +64,7 @@ def test_standing_wave_long_run_matches_oracle(m):
     dt = 0.9 / n
     st = I.standing_mode_1d_both_grids(m, n, dt, 3)
     got = gpu(m, n, dt, st, steps)
-    # long runs are judged against the oracle in extended precision: the binary64 oracle's
+    # long runs are compared with the oracle in extended precision: the binary64 oracle's
     # own rounding drifts about 2e-12 over 400 steps at m = 3
     ref = MO.run(m, n, dt, *st, steps, dtype=np.longdouble)
     for g, r in zip(got, ref):
