@@ -453,7 +453,7 @@ def run_aux(args, rank=0, world=1, dist=None):
         # the same run in the mixed modes (every shot has dt/h = 0.9, so one operator table serves all)
         modes = {}
         scale = float(p64.abs().max())
-        for name, mode in (("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP)):
+        for name, mode in (("fp32", hl.HL_FP32), ("fp32_comp", hl.HL_FP32_COMP), ("tc_split", hl.HL_TC_SPLIT)):
             ms_m, rc_m, best_m, _, pm = run_batch(mode)
             ms_m = max_over_ranks(ms_m, dist, "cuda")
             modes[name] = {"value": dof * lf / (ms_m / 1e3), "ms_per_run": ms_m, "tile": hl.TILES[best_m],
