@@ -8,8 +8,8 @@
 // Per tile (128 nodes of one grid row) and partner component ("unit"): 24 bulk
 // copies (6 digits x 2 slot chunks x 2 grid rows) into one of 3 shared-memory
 // stages; one lane issues 24 tcgen05.mma (6 data digits x 4 vertices, all levels
-// i + j <= 6 at once) into one of two TMEM accumulators; 8 epilogue warps (two
-// per TMEM lane quarter) combine the 7 levels in float-float, scale by the
+// i + j <= 6 at once) into one of two TMEM accumulators; 8 (p-half) or 16
+// (u-half) epilogue warps combine the 7 levels in float-float, scale by the
 // field exponent and add to the binary64 values.  K = 2 x 4 x 16 = 128 (p-half)
 // or 64 (u-half): one exact accumulation per tile.  The operator image of the
 // half (28 KB, build_tc5_images) stays in shared memory.
@@ -37,13 +37,18 @@ constexpr int kCh = 2;                       // 8-slot chunks (16 padded slots)
 constexpr int kRowBytes = kT5RX * 16;        // one copied digit row: 129 entries
 constexpr int kStages = 3;
 constexpr int kTxBytes = 24 * kRowBytes;
-// producer, MMA, 8 epilogue warps and 2 idle ones: at 10 or 12 warps the register file
-// gives 168 registers a thread either way (3 warps per sub-partition), and the compiler
-// fits the u-half's epilogue into them without spilling only at 12
-constexpr int kThreads = 384;
 constexpr int kEpiWarp0 = 2;
-constexpr int kEpiWarps = 8;                 // warps 2..9; warps 10 and 11 only reach the final barrier
-static_assert(kThreads / 32 >= kEpiWarp0 + kEpiWarps, "role layout");
+// Roles: warp 0 producer, warp 1 MMA, then EW epilogue warps, EW / 4 per TMEM lane quarter,
+// each owning 8 of the node's output columns (p-half: 16 columns, 8 warps, plus 2 idle warps
+// that only reach the final barrier, so that the register split gives 168 a thread; u-half:
+// 32 columns, 16 warps)
+template <bool PHALF>
+struct T2Roles {
+    static constexpr int EW = PHALF ? 8 : 16;
+    static constexpr int THREADS = PHALF ? 384 : 576;
+    static constexpr int NGRP = (PHALF ? 2 : 4) / (EW / 4);   // 8-column groups a thread
+    static_assert(THREADS / 32 >= kEpiWarp0 + EW && NGRP * (EW / 4) == (PHALF ? 2 : 4), "role layout");
+};
 constexpr int kSmemBytes = kT5BBytes + kStages * kT5ABytes + 8 * (2 * kStages + 5) + 16;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
@@ -70,7 +75,7 @@ __device__ __forceinline__ void mbar_arrive2(uint32_t mbar)
 // One half-step.  PHALF: X = p (NQ slots), partner digit planes of u (2
 // components); else X = u (2 directions), partner digit planes of p.
 template <int M, bool PHALF>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(T2Roles<PHALF>::THREADS, 1)
     k_half_tc2(const uint4 *__restrict__ G, double *__restrict__ X, int n0, int n1, int total_tiles,
                const uint4 *__restrict__ Bimg, const int *__restrict__ expo, const int *__restrict__ emaxp,
                int *emax_out, unsigned *status)
@@ -78,6 +83,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int NQ = (M + 1) * (M + 1);
     constexpr int NCIN = PHALF ? 2 : 1;
     using Op = T5Op<PHALF>;
+    using R = T2Roles<PHALF>;
     extern __shared__ __align__(1024) unsigned char t2_sm[];
     unsigned char *Bs = t2_sm;
     unsigned char *As = t2_sm + kT5BBytes;
@@ -102,14 +108,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_addr(acc_full + a), 1);
-            mbar_init(smem_addr(acc_empty + a), kEpiWarps * 32);
+            mbar_init(smem_addr(acc_empty + a), R::EW * 32);
         }
         mbar_init(smem_addr(drain), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     // the half's operator image, once per CTA
-    for (int e = tid; e < kT5BBytes / 16; e += kThreads) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(Bimg + e);
+    for (int e = tid; e < kT5BBytes / 16; e += R::THREADS) reinterpret_cast<uint4 *>(Bs)[e] = __ldg(Bimg + e);
     fence_async_smem();
     __syncthreads();
     tc_fence_after();
@@ -207,13 +213,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit(smem_addr(drain));
             mbar_wait(smem_addr(drain), 0u, kT5WaitLimit);
         }
-    } else if (warp < kEpiWarp0 + kEpiWarps) {
+    } else if (warp < kEpiWarp0 + R::EW) {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;                  // the TMEM lanes this warp may read
         const int half = (warp - kEpiWarp0) >> 2;      // which share of the node's outputs
         const int q = 32 * quarter + lane;             // node within the tile = TMEM lane
         const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
-        constexpr int NGRP = PHALF ? 1 : 2;            // groups of 8 output columns per thread
+        constexpr int NGRP = R::NGRP;                  // groups of 8 output columns per thread
         const int E = __ldg(emaxp) - 1022;
         int lt = 0, emx = 0;
         bool bad = false;
@@ -341,7 +347,7 @@ static cudaError_t run_tc2(const LaunchFp64 &a)
         }
         k_tc_cut<NQ, kCh><<<dim3(cut_x, (unsigned)n1, 2u), 128, 0, a.stream>>>(a.U, a.tc3_gu, 2, n0, n1, 1, emax_u);
         if ((e = cudaMemsetAsync(emax_p, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
-        k_half_tc2<M, true><<<grid, kThreads, kSmemBytes, a.stream>>>(a.tc3_gu, a.P, n0, n1, tiles, bp, a.tc_expo,
+        k_half_tc2<M, true><<<grid, T2Roles<true>::THREADS, kSmemBytes, a.stream>>>(a.tc3_gu, a.P, n0, n1, tiles, bp, a.tc_expo,
                                                                       emax_u, emax_p, a.status);
         if (src) {
             if ((e = launch_source(*a.src, a.shots, a.P, NQ, a.step0 + st, a.stream)) != cudaSuccess) return e;
@@ -351,7 +357,7 @@ static cudaError_t run_tc2(const LaunchFp64 &a)
         if (a.ev) cudaEventRecord(a.ev[2 * st + 1], a.stream);
         k_tc_cut<NQ, kCh><<<dim3(cut_x, (unsigned)n1, 1u), 128, 0, a.stream>>>(a.P, a.tc3_gp, 1, n0, n1, 1, emax_p);
         if ((e = cudaMemsetAsync(emax_u, 0, sizeof(int), a.stream)) != cudaSuccess) return e;
-        k_half_tc2<M, false><<<grid, kThreads, kSmemBytes, a.stream>>>(a.tc3_gp, a.U, n0, n1, tiles, bu,
+        k_half_tc2<M, false><<<grid, T2Roles<false>::THREADS, kSmemBytes, a.stream>>>(a.tc3_gp, a.U, n0, n1, tiles, bu,
                                                                        a.tc_expo + 16, emax_p, emax_u, a.status);
     }
     if (a.ev) cudaEventRecord(a.ev[2 * a.nsteps], a.stream);
