@@ -30,7 +30,7 @@
 //   warp 1, one lane (MMA): per unit 24 tcgen05.mma (6 data digits x 4 vertices,
 //     all levels i + j <= 6 at once) into one of two TMEM accumulators; after a
 //     group's two units, acc_full[acc];
-//   warps 2-9 (epilogue, two per TMEM lane quarter, 16 output columns each):
+//   warps 2-17 (epilogue, four per TMEM lane quarter, 8 output columns each):
 //     levels of a group to float-float, added to the running sums; after the last
 //     group of an output set, scale and add to the binary64 node values.
 // Every wait is bounded; on expiry the abort flag and the status bit
@@ -61,9 +61,12 @@ constexpr int kBBytes = kTc3UnitElems * 2; // operator digits of one unit (28672
 constexpr int kStageBytes = kT5ABytes + kBBytes;
 constexpr int kStages = 2;
 constexpr int kTxBytes = 24 * kRowBytes + kBBytes;
-constexpr int kThreads = 320;              // producer, MMA, 8 epilogue warps
 constexpr int kEpiWarp0 = 2;
-static_assert(kThreads == 32 * (kEpiWarp0 + 8), "role layout: every warp after the MMA warp is an epilogue warp");
+constexpr int kEpiWarps = 16;              // 4 per TMEM lane quarter, 8 of the 32 output columns each
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);   // producer, MMA, epilogue warps
+constexpr int kShares = kEpiWarps / 4;     // epilogue warps per lane quarter
+constexpr int kCG = 4 / kShares;           // 8-column groups a thread
+static_assert(kCG * kShares == 4, "role layout");
 constexpr int kAccCols = 7 * 32;           // one accumulator: 7 levels x 32 columns
 constexpr int kSmemBytes = kStages * kStageBytes + 8 * (4 * kStages + 1) + 16;
 static_assert(kTxBytes < (1 << 20), "transaction count");
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_addr(acc_full + a), 1);
-            mbar_init(smem_addr(acc_empty + a), 8 * 32);
+            mbar_init(smem_addr(acc_empty + a), kEpiWarps * 32);
         }
         mbar_init(smem_addr(drain), 1);
         *abort_flag = 0;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;                  // the TMEM lanes this warp may read
-        const int half = (warp - kEpiWarp0) >> 2;      // output columns 16 half .. 16 half + 15
+        const int share = (warp - kEpiWarp0) >> 2;     // output columns 8 kCG share ...
         const int q = 32 * quarter + lane;             // node within the tile = TMEM lane
         const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
         constexpr int GPS = PHALF ? 6 : 2;             // groups per output set
@@ -249,17 +252,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int gx = x0 + q;
             const bool mine = gx < n0;
             const int64_t node = (int64_t)gx + (int64_t)n0 * yz;
-            FF run[2][8];
-            double own[2][8];
+            FF run[kCG][8];
+            double own[kCG][8];
             bool quit = false;
             for (int g = 0; g < kGroups; ++g, ++gg) {
                 const int os = g / GPS;  // output set: 0 (p) or the direction of u
                 if (g % GPS == 0) {
 #pragma unroll
-                    for (int cg = 0; cg < 2; ++cg)
+                    for (int cg = 0; cg < kCG; ++cg)
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const int s = 16 * half + 8 * cg + j;
+                            const int s = 8 * (kCG * share + cg) + j;
                             run[cg][j] = FF{0.f, 0.f};
                             own[cg][j] = (mine && s < kNQ) ? X[(int64_t)(os * kNQ + s) * nnode + node] : 0.0;
                         }
@@ -273,8 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int cg = 0; cg < 2; ++cg) {
-                    const int col0 = 16 * half + 8 * cg;
+                for (int cg = 0; cg < kCG; ++cg) {
+                    const int col0 = 8 * (kCG * share + cg);
                     FF tot[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) tot[j] = FF{0.f, 0.f};
@@ -312,10 +315,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (g % GPS == GPS - 1 && mine) {
                     const int op = PHALF ? 0 : 1 + os;
 #pragma unroll
-                    for (int cg = 0; cg < 2; ++cg)
+                    for (int cg = 0; cg < kCG; ++cg)
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const int s = 16 * half + 8 * cg + j;
+                            const int s = 8 * (kCG * share + cg) + j;
                             if (s >= kNQ) continue;
                             const FF nrm = ff_two_sum(run[cg][j].hi, run[cg][j].lo);
                             const int k0 = E + __ldg(expo + op * 32 + s) - 14;
