@@ -31,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--init", choices=["gaussian", "random", "zero"], default="random")
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32_comp", "tc_split"], default="fp64")
     ap.add_argument("--tile", type=int, default=-1, help="tile shape index (HL_OPT_TILE); -1 keeps the default")
+    ap.add_argument("--split", action="store_true",
+                    help="FP64 half-steps as the split pair: interpolant stored, then evolved (HL_OPT_SPLIT)")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="instead of stepping: this many rows of MLP training steps (loss, gradient, Adam)")
     args = ap.parse_args(argv)
@@ -64,6 +66,8 @@ def main(argv=None):
             hl.hl_set_option(h, hl.HL_OPT_KERNEL_PATH, args.path)
         if args.tile >= 0:
             hl.hl_set_option(h, hl.HL_OPT_TILE, args.tile)
+        if args.split:
+            hl.hl_set_option(h, hl.HL_OPT_SPLIT, 1)
         hl.hl_set_precision(h, {"fp64": hl.HL_FP64, "fp32": hl.HL_FP32, "fp32_comp": hl.HL_FP32_COMP,
                                  "tc_split": hl.HL_TC_SPLIT}[args.precision])
         hl.hl_set_initial(h, p, u)
@@ -81,6 +85,7 @@ def main(argv=None):
         hl.hl_destroy(h)
     dof = (args.dim + 1) * (args.m + 1) ** args.dim * int(np.prod(ncell))
     print(json.dumps({"dim": args.dim, "m": args.m, "n_cells": ncell, "precision": args.precision, "tile": args.tile,
+                      "split": args.split,
                       "steps": args.steps, "ms": ms,
                       "ms_per_step": ms / max(args.steps, 1), "dof_updates_per_s": dof * args.steps / (ms / 1e3),
                       "status": status}))
