@@ -528,17 +528,30 @@ int hl_mlp_set_stream(hl_mlp *mlp, void *cuda_stream);
  * hl_mlp_params -- host copies of the parameters: get_params/get_grads
  * receive HL_MLP_NPARAMS floats (the gradients of the last hl_mlp_loss_grad);
  * set_params replaces the weights and resets Adam.  Any pointer may be NULL.
- * Synchronises the handle's stream.
+ * Synchronises the handle's stream; HL_ETIMEOUT if an earlier hl_mlp_forward
+ * reported an expired tensor-core wait.
  */
 int hl_mlp_params(hl_mlp *mlp, float *get_params, const float *set_params, float *get_grads);
 
-/* hl_mlp_forward -- Y_dev[rows][16] = network(X_dev[rows][288]). */
+/*
+ * hl_mlp_forward -- Y_dev[rows][16] = network(X_dev[rows][288]), on the
+ * network's stream.  With X_dev and Y_dev 16-byte aligned, one tcgen05 kernel
+ * runs all three layers per 128-row tile with the activations on chip (FP32
+ * accumulators in tensor memory); otherwise the per-layer GEMMs of
+ * hl_mlp_loss_grad run.  Both round the operands to BF16 and accumulate in
+ * FP32.  A bounded tensor-core wait that expires is reported as HL_ETIMEOUT by
+ * the next hl_mlp_params call, or hl_mlp_loss_grad call that returns a loss
+ * (the handle is then poisoned).
+ */
 int hl_mlp_forward(hl_mlp *mlp, const float *X_dev, int rows, float *Y_dev);
 
 /*
- * hl_mlp_loss_grad -- forward, loss against T_dev[rows][16] and the full
- * gradient (overwrites the previous one).  loss (host, may be NULL) receives
- * the mean squared error; passing it synchronises the stream.
+ * hl_mlp_loss_grad -- forward (as hl_mlp_forward; the tensor-core kernel
+ * also keeps the FP32 activations for the backward pass), loss against
+ * T_dev[rows][16] and the full gradient (overwrites the previous one) by
+ * per-layer GEMMs.  loss (host, may be NULL) receives the mean squared error;
+ * passing it synchronises the stream and reports an expired tensor-core wait
+ * (HL_ETIMEOUT).
  */
 int hl_mlp_loss_grad(hl_mlp *mlp, const float *X_dev, const float *T_dev, int rows, double *loss);
 
@@ -589,8 +602,9 @@ int hl_targets(const hl_solver *fine, int ratio, const hl_solver *coarse, const 
 
 /*
  * hl_apply_correction -- p~(J) += out_scale * network(features(J)) at every
- * primal node of the coarse solver (the addition in FP64).  Uses workspace
- * owned by the network handle.
+ * primal node of the coarse solver (the addition in FP64; the network as
+ * hl_mlp_forward).  Uses workspace owned by the network handle.  An expired
+ * tensor-core wait is reported by the solver's next hl_sync as HL_ETIMEOUT.
  */
 int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_scale, float t_feature, double out_scale);
 

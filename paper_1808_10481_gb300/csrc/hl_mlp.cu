@@ -10,13 +10,20 @@
 //   y = relu(relu(x W1 + b1) W2 + b2) W3 + b3            288 -> 128 -> 128 -> 16
 //   p~(J) += out_scale * y   (added in FP64)
 //
-// Every matrix product runs on the tensor cores through a warp-level
-// mma.sync m16n8k16 with BF16 operands (weights and activations rounded to
-// BF16 when staged) and FP32 accumulation; master weights, Adam moments and
-// activations are FP32.  Loss: mean over rows and outputs of (y - target)^2.
+// Every matrix product runs on the tensor cores with BF16 operands (weights
+// and activations rounded to nearest BF16 when staged) and FP32 accumulation.
+// The forward runs all three layers of a 128-row tile in one tcgen05 kernel
+// (k_mlp_forward_tc, accumulators in tensor memory); the backward's GEMMs,
+// whose operands are transposed views and whose weight gradients reduce over
+// the batch (split-K), use the warp-level mma.sync m16n8k16 (k_gemm), which
+// also serves the forward when a buffer is not 16-byte aligned.  Master
+// weights, Adam moments and activations are FP32.  Loss: mean over rows and
+// outputs of (y - target)^2.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -26,6 +33,7 @@
 
 #include "../../include/hl.h"
 #include "hl_internal.h"
+#include "hl_sm100.cuh"
 #include "hl_solver.h"
 
 namespace hl {
@@ -262,6 +270,244 @@ static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K
 }
 
 // ---------------------------------------------------------------------------
+// Inference forward on the fifth-generation tensor cores (tcgen05): all three
+// layers of one 128-row tile in one kernel, activations kept on chip (TMEM
+// accumulators, BF16 operands in shared memory); only X is read and Y written.
+//
+// Persistent: one CTA of 256 threads per SM walks the row tiles.  Each CTA
+// rounds the weights to BF16 once into shared memory as the B operands (N x K,
+// K-major).  Per tile:
+//   X rows (FP32 in HBM, coalesced float4) -> BF16 A operand;
+//   one thread issues 18 MMAs (K = 16 each) into TMEM columns 0..127;
+//   epilogue (all 8 warps: warp w reads TMEM lanes 32 (w % 4).., half w / 4 of
+//   the columns) adds b1, applies ReLU and rounds to BF16 into H1, the next
+//   A operand, in the X tile's space;
+//   8 MMAs into columns 128..255 -> H2;  8 MMAs (N = 16) into columns 0..15;
+//   warps 0..3 add b3 and write the Y rows.
+// For training, the FP32 activations H1 and H2 (after bias and ReLU, before the
+// BF16 rounding) can also be written out, for the backward GEMMs.
+// Operand layout (no swizzle): the 8-value K chunk c of row r sits at byte
+// c * (rows * 16) + r * 16; the descriptor's K stride (LBO) is one chunk and
+// its 8-row stride (SBO) 128 bytes.  The rounding points are k_gemm's:
+// operands rounded to nearest BF16, FP32 accumulation, bias and ReLU in FP32
+// before the next layer's rounding.  Every mbarrier wait is bounded; on expiry
+// the kernel sets kStatusTimeout in *status (if given), all threads leave the
+// tile loop together and the MMAs in flight are drained before TMEM is freed.
+constexpr int kFwdRows = 128;                         // MMA M: rows per tile
+constexpr int kFwdThreads = 256;
+constexpr int kFwdChunk = kFwdRows * 16;              // one 8-wide K chunk of a 128-row operand (bytes)
+constexpr int kFwdXBytes = (kIn / 8) * kFwdChunk;     // the X tile; H1 and H2 reuse its space
+constexpr int kFwdOffW1 = kFwdXBytes;
+constexpr int kFwdOffW2 = kFwdOffW1 + (kIn / 8) * kH * 16;
+constexpr int kFwdOffW3 = kFwdOffW2 + (kH / 8) * kH * 16;
+constexpr int kFwdOffBias = kFwdOffW3 + (kH / 8) * kOut * 16;
+constexpr int kFwdOffBar = kFwdOffBias + (2 * kH + kOut) * 4;
+constexpr int kFwdSmem = kFwdOffBar + 32;             // two mbarriers, the TMEM address
+constexpr int kFwdTmemCols = 2 * kH;                  // layer 1 (and 3) at 0, layer 2 at kH
+static_assert(kIn % 16 == 0 && kH % 16 == 0 && kOut % 16 == 0 && kOut >= 16, "MMA K and N shapes");
+static_assert(kH == kFwdRows, "the hidden width is the A operand's row count of layers 2 and 3");
+static_assert(2 * (kH / 8) * kFwdChunk <= kFwdXBytes, "H1 and H2 fit in the X tile's space");
+static_assert(kFwdOffBar % 8 == 0 && kFwdSmem <= 227 * 1024, "shared-memory layout");
+
+// B operand (n, k) = W[k][n] of a row-major K x N weight matrix, rounded to BF16
+__device__ __forceinline__ void fwd_stage_weight(unsigned char *dst, const float *__restrict__ W, int K, int N,
+                                                 int tid)
+{
+    const int units = (K / 8) * N;
+    for (int u = tid; u < units; u += kFwdThreads) {
+        const int c = u / N, n = u % N;
+        const float *w = W + (int64_t)(8 * c) * N + n;
+        const uint4 v = make_uint4(pack2(__ldg(w), __ldg(w + N)), pack2(__ldg(w + 2 * N), __ldg(w + 3 * N)),
+                                   pack2(__ldg(w + 4 * N), __ldg(w + 5 * N)), pack2(__ldg(w + 6 * N), __ldg(w + 7 * N)));
+        *reinterpret_cast<uint4 *>(dst + c * (N * 16) + n * 16) = v;
+    }
+}
+
+// A operand (r, k) = X[row0 + r][k] rounded to BF16, rows at or past `rows` zero.  A warp
+// moves 8 rows x 16 floats at a time: 16 fully used 32-byte sectors per load, and its
+// shared-memory stores fill two 128-byte K chunks without bank conflicts.
+__device__ __forceinline__ void fwd_stage_x(unsigned char *dst, const float *__restrict__ X, int64_t row0, int rows,
+                                            int warp, int lane)
+{
+    constexpr int CG = kIn / 16;                               // 16-float groups per row
+    constexpr int PER = (kFwdRows / 8) * CG / (kFwdThreads / 32);
+    constexpr int BATCH = 12;                                  // loads in flight per thread
+    static_assert((kFwdRows / 8) * CG % (kFwdThreads / 32) == 0 && PER % BATCH == 0, "X staging split");
+    const int ri = lane >> 2, ci = lane & 3;
+#pragma unroll 1
+    for (int i0 = 0; i0 < PER; i0 += BATCH) {
+        float4 x[BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int u = warp + (i0 + j) * (kFwdThreads / 32);
+            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + ci;
+            x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row0 + r < rows) x[j] = __ldg(reinterpret_cast<const float4 *>(X + (row0 + r) * kIn) + c4);
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int u = warp + (i0 + j) * (kFwdThreads / 32);
+            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + ci;
+            *reinterpret_cast<uint2 *>(dst + (c4 >> 1) * kFwdChunk + r * 16 + (c4 & 1) * 8) =
+                make_uint2(pack2(x[j].x, x[j].y), pack2(x[j].z, x[j].w));
+        }
+    }
+}
+
+// 64 accumulator columns [c0, c0 + 64) of this thread's row r: + bias, ReLU, BF16 into
+// the next layer's A operand (K = kH); the FP32 activations also to hout (row of kH
+// floats; NULL = not kept)
+__device__ __forceinline__ void fwd_epi_hidden(uint32_t tacc, int c0, const float *bias, unsigned char *dst, int r,
+                                               float *hout)
+{
+    float v[4][16];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) tmem_ld16(tacc + (uint32_t)(c0 + 16 * g), v[g]);
+    tmem_ld_wait();
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int c = c0 + 16 * g;
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[g][j] = fmaxf(v[g][j] + bias[c + j], 0.f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = pack2(v[g][2 * j], v[g][2 * j + 1]);
+        if (hout) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                reinterpret_cast<float4 *>(hout + c)[j] =
+                    make_float4(v[g][4 * j], v[g][4 * j + 1], v[g][4 * j + 2], v[g][4 * j + 3]);
+        }
+        *reinterpret_cast<uint4 *>(dst + (c / 8) * kFwdChunk + r * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(dst + (c / 8 + 1) * kFwdChunk + r * 16) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
+    k_mlp_forward_tc(const float *__restrict__ X, int rows, const float *__restrict__ W1,
+                     const float *__restrict__ b1, const float *__restrict__ W2, const float *__restrict__ b2,
+                     const float *__restrict__ W3, const float *__restrict__ b3, float *__restrict__ Y,
+                     float *__restrict__ H1out, float *__restrict__ H2out, unsigned *status)
+{
+    extern __shared__ __align__(1024) unsigned char fw_sm[];
+    unsigned char *As = fw_sm;                                  // X tile; then H1 and H2
+    unsigned char *H1s = fw_sm, *H2s = fw_sm + (kH / 8) * kFwdChunk;
+    unsigned char *W1s = fw_sm + kFwdOffW1, *W2s = fw_sm + kFwdOffW2, *W3s = fw_sm + kFwdOffW3;
+    float *bias = reinterpret_cast<float *>(fw_sm + kFwdOffBias);   // b1, b2, b3
+    uint64_t *bar = reinterpret_cast<uint64_t *>(fw_sm + kFwdOffBar), *drain = bar + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles = (rows + kFwdRows - 1) / kFwdRows;
+
+    if (warp == 0) {
+        tmem_alloc(smem_addr(tmem_slot), kFwdTmemCols);
+        tc_fence_before();
+    }
+    if (tid == 32) {
+        mbar_init(smem_addr(bar), 1);
+        mbar_init(smem_addr(drain), 1);
+    }
+    fwd_stage_weight(W1s, W1, kIn, kH, tid);
+    fwd_stage_weight(W2s, W2, kH, kH, tid);
+    fwd_stage_weight(W3s, W3, kH, kOut, tid);
+    for (int i = tid; i < kH; i += kFwdThreads) {
+        bias[i] = __ldg(b1 + i);
+        bias[kH + i] = __ldg(b2 + i);
+    }
+    if (tid < kOut) bias[2 * kH + tid] = __ldg(b3 + tid);
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = 32 * quarter + lane;                          // row of the tile = TMEM lane
+    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
+    const uint32_t sA = smem_addr(As), sH1 = smem_addr(H1s), sH2 = smem_addr(H2s);
+    const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s), sW3 = smem_addr(W3s);
+    constexpr uint32_t idH = umma_idesc_bf16(kFwdRows, kH), idO = umma_idesc_bf16(kFwdRows, kOut);
+    uint32_t phase = 0;
+    // every thread waits for the committed MMAs; a wait that expires is recorded and
+    // the tile loop is left by all threads at the next barrier (__syncthreads_or).  The
+    // result is made warp-uniform, since the TMEM loads that follow are warp-collective.
+    auto wait_mma = [&]() -> bool {
+        const bool ok = mbar_wait(smem_addr(bar), phase, kMbarWaitLimit);
+        phase ^= 1u;
+        if (!ok && status) atomicOr(status, kStatusTimeout);
+        tc_fence_after();
+        return __all_sync(0xFFFFFFFFu, ok);
+    };
+
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t row0 = (int64_t)t * kFwdRows;
+        fwd_stage_x(As, X, row0, rows, warp, lane);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int s = 0; s < kIn / 16; ++s)
+                umma_bf16(tmem, umma_desc(sA + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                          umma_desc(sW1 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
+            umma_commit(smem_addr(bar));
+        }
+        bool fail = !wait_mma();
+        const bool keep = row0 + r < rows;
+        if (!fail) fwd_epi_hidden(tl, 64 * half, bias, H1s, r, H1out && keep ? H1out + (row0 + r) * kH : nullptr);
+        fence_async_smem();
+        tc_fence_before();
+        if (__syncthreads_or(fail)) break;
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int s = 0; s < kH / 16; ++s)
+                umma_bf16(tmem + kH, umma_desc(sH1 + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                          umma_desc(sW2 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
+            umma_commit(smem_addr(bar));
+        }
+        fail = !wait_mma();
+        if (!fail)
+            fwd_epi_hidden(tl + kH, 64 * half, bias + kH, H2s, r, H2out && keep ? H2out + (row0 + r) * kH : nullptr);
+        fence_async_smem();
+        tc_fence_before();
+        if (__syncthreads_or(fail)) break;
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int s = 0; s < kH / 16; ++s)
+                umma_bf16(tmem, umma_desc(sH2 + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                          umma_desc(sW3 + (uint32_t)(s * 2 * kOut * 16), kOut * 16, 128), idO, s > 0 ? 1u : 0u);
+            umma_commit(smem_addr(bar));
+        }
+        fail = !wait_mma();
+        if (!fail && half == 0) {
+            float v[16];
+            tmem_ld16(tl, v);
+            tmem_ld_wait();
+            if (row0 + r < rows) {
+                float4 *y = reinterpret_cast<float4 *>(Y + (row0 + r) * kOut);
+                const float *bo = bias + 2 * kH;
+#pragma unroll
+                for (int j = 0; j < kOut / 4; ++j)
+                    y[j] = make_float4(v[4 * j] + bo[4 * j], v[4 * j + 1] + bo[4 * j + 1], v[4 * j + 2] + bo[4 * j + 2],
+                                       v[4 * j + 3] + bo[4 * j + 3]);
+            }
+        }
+        tc_fence_before();
+        if (__syncthreads_or(fail)) break;
+    }
+    // every MMA issued has completed before the tensor memory is released
+    if (tid == 0) {
+        umma_commit(smem_addr(drain));
+        if (!mbar_wait(smem_addr(drain), 0u, kMbarWaitLimit) && status) atomicOr(status, kStatusTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kFwdTmemCols);
+}
+
+// ---------------------------------------------------------------------------
 // elementwise and reduction kernels
 __global__ void k_mse(const float *__restrict__ Y, const float *__restrict__ T, float *__restrict__ dY, int64_t n,
                       double *loss)
@@ -437,6 +683,36 @@ static constexpr int64_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (int64_t)kIn * kH, OFF_W2
                          N_PARAMS = OFF_B3 + kOut;
 static_assert(N_PARAMS == HL_MLP_NPARAMS, "parameter count and header disagree");
 
+// Y (and, if not NULL, the activations H1, H2) = forward(X) by k_mlp_forward_tc when every
+// buffer is 16-byte aligned (rows of kIn, kH and kOut floats keep that alignment); *used
+// tells the caller whether it ran.
+static cudaError_t forward_fused(const float *w, const float *X, int rows, float *Y, float *H1, float *H2,
+                                 unsigned *status, cudaStream_t st, bool *used)
+{
+    *used = false;
+    if (rows <= 0) return cudaSuccess;
+    if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || ((uintptr_t)H1 & 15) || ((uintptr_t)H2 & 15))
+        return cudaSuccess;
+    static std::atomic<uint64_t> opted_in{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(opted_in.load() & bit)) {
+        if ((e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem)) !=
+            cudaSuccess)
+            return e;
+        opted_in.fetch_or(bit);
+    }
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int tiles = (rows + kFwdRows - 1) / kFwdRows;
+    k_mlp_forward_tc<<<(unsigned)std::min(tiles, sms), kFwdThreads, kFwdSmem, st>>>(
+        X, rows, w + OFF_W1, w + OFF_B1, w + OFF_W2, w + OFF_B2, w + OFF_W3, w + OFF_B3, Y, H1, H2, status);
+    *used = true;
+    return cudaGetLastError();
+}
+
 struct hl_mlp {
     float *w = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // N_PARAMS each
     float *work = nullptr;   // per-row activations: H1, H2, Y, dY, dH2, dH1
@@ -444,6 +720,7 @@ struct hl_mlp {
     int64_t rows_cap = 0;
     double *loss = nullptr;  // device
     double *loss_host = nullptr;
+    unsigned *status = nullptr;  // device status word of the tensor-core forward (kStatusTimeout)
     int64_t adam_t = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -477,6 +754,20 @@ static int mlp_check(hl_mlp *h)
     if (h->poisoned) return mlp_err(h, HL_ESTATE, "mlp handle poisoned: " + h->err);
     return HL_OK;
 }
+
+// after a stream synchronisation: a bounded wait of hl_mlp_forward's tensor-core
+// kernel that expired poisons the handle
+static int mlp_status(hl_mlp *h)
+{
+    unsigned st = 0;
+    MLP_CK(h, cudaMemcpy(&st, h->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) {
+        h->poisoned = true;
+        return mlp_err(h, HL_ETIMEOUT, "a bounded wait on the tensor cores expired (handle poisoned)");
+    }
+    return HL_OK;
+}
+
 
 // rows x (H1, H2, Y, dY, dH2, dH1)
 static int ensure_rows(hl_mlp *h, int64_t rows)
@@ -525,6 +816,16 @@ static cudaError_t forward_into(hl_mlp *h, const float *X, int rows, const Work 
     return gemm({w.H2, kH, 1}, {h->w + OFF_W3, kOut, 1}, Y, kOut, rows, kOut, kH, h->w + OFF_B3, 0, st);
 }
 
+// the network applied to rows of X: the fused tensor-core kernel, or the three GEMMs
+// when X or Y is not 16-byte aligned
+static cudaError_t forward_any(hl_mlp *h, const float *X, int rows, float *Y, unsigned *status, cudaStream_t st)
+{
+    bool used = false;
+    cudaError_t e = forward_fused(h->w, X, rows, Y, nullptr, nullptr, status, st, &used);
+    if (e != cudaSuccess || used) return e;
+    return forward_into(h, X, rows, work_ptrs(h, rows), Y, st);
+}
+
 extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
 {
     if (!out) return mlp_err(nullptr, HL_EINVAL, "out is NULL");
@@ -537,6 +838,7 @@ extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
         (e = cudaMalloc(&h->m2, N_PARAMS * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->loss, sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&h->splitk, kSplitKFloats * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->status, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMallocHost(&h->loss_host, sizeof(double))) != cudaSuccess) {
         std::string msg = std::string("mlp set-up failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -553,7 +855,8 @@ extern "C" int hl_mlp_create(uint64_t seed, hl_mlp **out)
     if ((e = cudaMemcpy(h->w, w.data(), N_PARAMS * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(h->g, 0, N_PARAMS * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(h->m1, 0, N_PARAMS * sizeof(float))) != cudaSuccess ||
-        (e = cudaMemset(h->m2, 0, N_PARAMS * sizeof(float))) != cudaSuccess) {
+        (e = cudaMemset(h->m2, 0, N_PARAMS * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(h->status, 0, sizeof(unsigned))) != cudaSuccess) {
         std::string msg = std::string("mlp set-up failed: ") + cudaGetErrorString(e);
         hl_mlp_destroy(h);
         return mlp_err(nullptr, HL_ECUDA, msg);
@@ -572,6 +875,7 @@ extern "C" void hl_mlp_destroy(hl_mlp *h)
     cudaFree(h->m2);
     cudaFree(h->work);
     cudaFree(h->splitk);
+    cudaFree(h->status);
     cudaFree(h->loss);
     if (h->loss_host) cudaFreeHost(h->loss_host);
     delete h;
@@ -593,6 +897,7 @@ extern "C" int hl_mlp_params(hl_mlp *h, float *get_params, const float *set_para
     int rc = mlp_check(h);
     if (rc) return rc;
     MLP_CK(h, cudaStreamSynchronize(h->stream));
+    if ((rc = mlp_status(h))) return rc;
     if (set_params) {
         MLP_CK(h, cudaMemcpy(h->w, set_params, N_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
         MLP_CK(h, cudaMemset(h->m1, 0, N_PARAMS * sizeof(float)));
@@ -612,7 +917,7 @@ extern "C" int hl_mlp_forward(hl_mlp *h, const float *X_dev, int rows, float *Y_
     if (rows == 0) return HL_OK;
     rc = ensure_rows(h, rows);
     if (rc) return rc;
-    MLP_CK(h, forward_into(h, X_dev, rows, work_ptrs(h, rows), Y_dev, h->stream));
+    MLP_CK(h, forward_any(h, X_dev, rows, Y_dev, h->status, h->stream));
     return HL_OK;
 }
 
@@ -625,7 +930,9 @@ extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_de
     if (rc) return rc;
     const Work w = work_ptrs(h, rows);
     const cudaStream_t st = h->stream;
-    MLP_CK(h, forward_into(h, X_dev, rows, w, w.Y, h->stream));
+    bool fused = false;   // the tensor-core forward keeps H1 and H2 for the backward GEMMs
+    MLP_CK(h, forward_fused(h->w, X_dev, rows, w.Y, w.H1, w.H2, h->status, st, &fused));
+    if (!fused) MLP_CK(h, forward_into(h, X_dev, rows, w, w.Y, st));
     MLP_CK(h, cudaMemsetAsync(h->loss, 0, sizeof(double), st));
     const int64_t ny = (int64_t)rows * kOut;
     k_mse<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, T_dev, w.dY, ny, h->loss);
@@ -650,6 +957,7 @@ extern "C" int hl_mlp_loss_grad(hl_mlp *h, const float *X_dev, const float *T_de
     if (loss) {
         MLP_CK(h, cudaMemcpyAsync(h->loss_host, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         MLP_CK(h, cudaStreamSynchronize(st));
+        if ((rc = mlp_status(h))) return rc;
         *loss = *h->loss_host;
     }
     return HL_OK;
@@ -784,7 +1092,7 @@ extern "C" int hl_apply_correction(hl_solver *coarse, hl_mlp *mlp, float feat_sc
     k_features<<<(unsigned)((nx + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, coarse->u, (int)s.n[0], (int)s.n[1],
                                                                        s.nnode, nullptr, rows, feat_scale, t_feature, X);
     MLP_CK(mlp, cudaGetLastError());
-    MLP_CK(mlp, forward_into(mlp, X, rows, w, w.Y, mlp->stream));
+    MLP_CK(mlp, forward_any(mlp, X, rows, w.Y, coarse->status, mlp->stream));
     const int64_t ny = (int64_t)rows * kOut;
     k_correct<<<(unsigned)((ny + 255) / 256), 256, 0, mlp->stream>>>(coarse->p, s.nnode, w.Y, rows, out_scale);
     MLP_CK(mlp, cudaGetLastError());
@@ -866,7 +1174,7 @@ cudaError_t apply_correction_checked(hl_solver *h, cudaStream_t st)
                                                               rows, h->corr_feat_scale, h->corr_t_feature, X);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = forward_into(mlp, X, rows, w, w.Y, st)) != cudaSuccess) return e;
+    if ((e = forward_any(mlp, X, rows, w.Y, h->status, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->corr_sums, 0, 2 * sizeof(double), st)) != cudaSuccess) return e;
     const int64_t ny = (int64_t)rows * kOut;
     k_corr_norms<<<blocks_for(ny, 256), 256, 0, st>>>(w.Y, h->p, h->corr_snap, s.nnode, h->corr_out_scale,

@@ -21,6 +21,9 @@
 
 namespace hl {
 
+constexpr uint32_t kMbarWaitLimit = 1u << 22;  // polls of an mbarrier before giving up
+constexpr unsigned kStatusTimeout = 2u;        // status-word bit: a bounded wait expired
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor (no swizzle, version 1 of the sm_100 format).

@@ -60,8 +60,7 @@ constexpr int kT5Chunk = kT5RowsPad * 16;     // bytes of one 8-slot plane: 264 
 constexpr int kT5Plane = 2 * kT5Chunk;        // one digit of one component (16 slots)
 constexpr int kT5ABytes = kT5Digits * kT5Plane;
 constexpr int kT5BBytes = 28672;              // operator image of one half-step (either half)
-constexpr uint32_t kT5WaitLimit = 1u << 22;   // polls of an mbarrier before giving up
-constexpr unsigned kStatusTimeout = 2u;       // status bit: a bounded wait expired
+constexpr uint32_t kT5WaitLimit = kMbarWaitLimit;
 
 // Operator image of one half (host-built, build_tc5_images): blocks kb of
 // [2 chunks][7 NPL rows][8 BF16], kb = component * 4 + vertex (p-half, NPL = 16)

@@ -35,6 +35,8 @@ def main(argv=None):
                     help="FP64 half-steps as the split pair: interpolant stored, then evolved (HL_OPT_SPLIT)")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="instead of stepping: this many rows of MLP training steps (loss, gradient, Adam)")
+    ap.add_argument("--mlp-forward", action="store_true",
+                    help="with --mlp-rows: time the inference forward (hl_mlp_forward) instead of training steps")
     args = ap.parse_args(argv)
     if args.mlp_rows:
         return run_mlp(args)
@@ -105,6 +107,8 @@ def run_mlp(args):
     X = torch.from_numpy(rng.standard_normal((rows, hl.HL_MLP_IN)).astype(np.float32)).cuda()
     T = torch.from_numpy(rng.standard_normal((rows, hl.HL_MLP_OUT)).astype(np.float32)).cuda()
     net = hl.hl_mlp_create(args.seed)
+    if args.mlp_forward:
+        return run_mlp_forward(args, hl, net, X, rows)
     try:
         stream = torch.cuda.current_stream()
         hl.hl_mlp_set_stream(net, stream)
@@ -124,6 +128,33 @@ def run_mlp(args):
     flops = 3 * 2 * rows * (hl.HL_MLP_IN * hl.HL_MLP_HIDDEN + hl.HL_MLP_HIDDEN ** 2 + hl.HL_MLP_HIDDEN * hl.HL_MLP_OUT)
     print(json.dumps({"mlp_rows": rows, "steps": args.steps, "ms_per_step": ms / max(args.steps, 1),
                       "tflops": flops * args.steps / (ms / 1e3) / 1e12, "loss": loss}))
+    return 0
+
+
+def run_mlp_forward(args, hl, net, X, rows):
+    """Inference forwards of `rows` rows: X read once, Y written (the correction's network call)."""
+    import torch
+
+    Y = torch.empty((rows, hl.HL_MLP_OUT), dtype=torch.float32, device=X.device)
+    try:
+        stream = torch.cuda.current_stream()
+        hl.hl_mlp_set_stream(net, stream)
+        for _ in range(args.warmup):
+            hl.hl_mlp_forward(net, X, rows, Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            hl.hl_mlp_forward(net, X, rows, Y)
+        e1.record(stream)
+        hl.hl_mlp_params(net)          # synchronises and reports an expired tensor-core wait
+        ms = e0.elapsed_time(e1)
+    finally:
+        hl.hl_mlp_destroy(net)
+    flops = 2 * rows * (hl.HL_MLP_IN * hl.HL_MLP_HIDDEN + hl.HL_MLP_HIDDEN ** 2 + hl.HL_MLP_HIDDEN * hl.HL_MLP_OUT)
+    nbytes = rows * 4 * (hl.HL_MLP_IN + hl.HL_MLP_OUT)
+    us = 1e3 * ms / max(args.steps, 1)
+    print(json.dumps({"mlp_rows": rows, "forward": True, "steps": args.steps, "us_per_forward": us,
+                      "gbs": nbytes / (us / 1e6) / 1e9, "tflops": flops / (us / 1e6) / 1e12}))
     return 0
 
 

@@ -141,6 +141,24 @@ def test_forward_matches_oracle_elementwise(net):
     check_elementwise("Y", Yd.cpu().numpy(), Y_ref, eY, mag)
 
 
+@pytest.mark.parametrize("rows,offset", [(2 * 152 * 128 + 77, 0), (333, 1)])
+def test_forward_paths_match_oracle_elementwise(net, rows, offset):
+    """Both forward paths against the oracle, element by element.  offset 0: the tcgen05
+    kernel with 305 tiles of 128 rows, so its persistent CTAs (one per SM) take up to three
+    tiles each, the last one ragged.  offset 1: X starts one float past a 16-byte boundary,
+    which sends the call to the per-layer GEMMs."""
+    X, _ = _batch(rows, 2)
+    buf = torch.zeros(rows * M.N_IN + offset, dtype=torch.float32, device=DEV)
+    buf[offset:] = torch.from_numpy(X.ravel()).to(DEV)
+    Yd = torch.full((rows, M.N_OUT), float("nan"), dtype=torch.float32, device=DEV)
+    hl.hl_mlp_forward(net, buf[offset:], rows, Yd)
+    torch.cuda.synchronize()
+    params, _ = hl.hl_mlp_params(net)
+    P = unpack(params)
+    Y_ref, eY, mag, _ = forward_reference(P, X.astype(np.float64))
+    check_elementwise("Y", Yd.cpu().numpy(), Y_ref, eY, mag)
+
+
 def test_gradients_match_oracle_elementwise(net):
     rows = 517
     X, T = _batch(rows, 2)
