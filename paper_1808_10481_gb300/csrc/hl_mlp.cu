@@ -270,20 +270,22 @@ static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K
 }
 
 // ---------------------------------------------------------------------------
-// Inference forward on the fifth-generation tensor cores (tcgen05): all three
-// layers of one 128-row tile in one kernel, activations kept on chip (TMEM
-// accumulators, BF16 operands in shared memory); only X is read and Y written.
+// Forward on the fifth-generation tensor cores (tcgen05): all three layers of
+// one 128-row tile in one kernel, activations kept on chip (TMEM accumulators,
+// BF16 operands in shared memory); only X is read and Y written.
 //
-// Persistent: one CTA of 256 threads per SM walks the row tiles.  Each CTA
-// rounds the weights to BF16 once into shared memory as the B operands (N x K,
-// K-major).  Per tile:
-//   X rows (FP32 in HBM, coalesced float4) -> BF16 A operand;
-//   one thread issues 18 MMAs (K = 16 each) into TMEM columns 0..127;
-//   epilogue (all 8 warps: warp w reads TMEM lanes 32 (w % 4).., half w / 4 of
-//   the columns) adds b1, applies ReLU and rounds to BF16 into H1, the next
-//   A operand, in the X tile's space;
-//   8 MMAs into columns 128..255 -> H2;  8 MMAs (N = 16) into columns 0..15;
-//   warps 0..3 add b3 and write the Y rows.
+// Persistent and warp-specialised: one CTA of 17 warps per SM walks the row
+// tiles; its roles hand each tile along mbarriers.
+//   producers (warps 8..15): X rows (FP32 in HBM, coalesced float4) -> the BF16
+//     A operand in the X buffer -> x_full.  They start the next tile as soon as
+//     the tile's layer-1 MMAs have read the buffer (x_empty), so the HBM reads
+//     overlap the rest of the tile.
+//   MMA (lane 0 of warp 16): 18 MMAs (K = 16) into TMEM columns 0..127 ->
+//     x_empty, acc1;  after h1: 8 MMAs into 128..255 -> acc2;  after h2: 8
+//     MMAs (N = 16) into 256..271 -> acc3.
+//   epilogue (warps 0..7; warp w reads TMEM lanes 32 (w % 4).. and half w / 4
+//     of the columns): acc1 + b1, ReLU, BF16 -> H (the next A operand) -> h1;
+//     acc2 -> H again (layer 2 has read H1 by then) -> h2;  acc3 + b3 -> Y.
 // For training, the FP32 activations H1 and H2 (after bias and ReLU, before the
 // BF16 rounding) can also be written out, for the backward GEMMs.
 // Operand layout (no swizzle): the 8-value K chunk c of row r sits at byte
@@ -291,22 +293,27 @@ static cudaError_t gemm(Mat A, Mat B, float *C, int64_t ldc, int M, int N, int K
 // its 8-row stride (SBO) 128 bytes.  The rounding points are k_gemm's:
 // operands rounded to nearest BF16, FP32 accumulation, bias and ReLU in FP32
 // before the next layer's rounding.  Every mbarrier wait is bounded; on expiry
-// the kernel sets kStatusTimeout in *status (if given), all threads leave the
-// tile loop together and the MMAs in flight are drained before TMEM is freed.
+// the thread sets kStatusTimeout in *status (if given) and an abort flag that
+// every role checks, all roles leave their loops, and the MMAs in flight are
+// drained before TMEM is freed.
 constexpr int kFwdRows = 128;                         // MMA M: rows per tile
-constexpr int kFwdThreads = 256;
+constexpr int kFwdEpiWarps = 8, kFwdProdWarps = 8;
+constexpr int kFwdMmaWarp = kFwdEpiWarps + kFwdProdWarps;
+constexpr int kFwdThreads = 32 * (kFwdMmaWarp + 1);
+constexpr int kFwdEpiThreads = 32 * kFwdEpiWarps, kFwdProdThreads = 32 * kFwdProdWarps;
 constexpr int kFwdChunk = kFwdRows * 16;              // one 8-wide K chunk of a 128-row operand (bytes)
-constexpr int kFwdXBytes = (kIn / 8) * kFwdChunk;     // the X tile; H1 and H2 reuse its space
-constexpr int kFwdOffW1 = kFwdXBytes;
+constexpr int kFwdOffH = (kIn / 8) * kFwdChunk;       // after the X buffer: H1, then H2, in one buffer
+constexpr int kFwdOffW1 = kFwdOffH + (kH / 8) * kFwdChunk;
 constexpr int kFwdOffW2 = kFwdOffW1 + (kIn / 8) * kH * 16;
 constexpr int kFwdOffW3 = kFwdOffW2 + (kH / 8) * kH * 16;
 constexpr int kFwdOffBias = kFwdOffW3 + (kH / 8) * kOut * 16;
 constexpr int kFwdOffBar = kFwdOffBias + (2 * kH + kOut) * 4;
-constexpr int kFwdSmem = kFwdOffBar + 32;             // two mbarriers, the TMEM address
-constexpr int kFwdTmemCols = 2 * kH;                  // layer 1 (and 3) at 0, layer 2 at kH
+constexpr int kFwdBars = 8;                           // x_full x_empty acc1 h1 acc2 h2 acc3 drain
+constexpr int kFwdSmem = kFwdOffBar + 8 * kFwdBars + 16;   // + abort flag, TMEM address
+constexpr int kFwdTmemCols = 512;                     // acc1 at 0, acc2 at kH, acc3 at 2 kH
 static_assert(kIn % 16 == 0 && kH % 16 == 0 && kOut % 16 == 0 && kOut >= 16, "MMA K and N shapes");
 static_assert(kH == kFwdRows, "the hidden width is the A operand's row count of layers 2 and 3");
-static_assert(2 * (kH / 8) * kFwdChunk <= kFwdXBytes, "H1 and H2 fit in the X tile's space");
+static_assert(2 * kH + kOut <= kFwdTmemCols, "accumulators fit the allocated TMEM columns");
 static_assert(kFwdOffBar % 8 == 0 && kFwdSmem <= 227 * 1024, "shared-memory layout");
 
 // B operand (n, k) = W[k][n] of a row-major K x N weight matrix, rounded to BF16
@@ -323,32 +330,32 @@ __device__ __forceinline__ void fwd_stage_weight(unsigned char *dst, const float
     }
 }
 
-// A operand (r, k) = X[row0 + r][k] rounded to BF16, rows at or past `rows` zero.  A warp
-// moves 8 rows x 16 floats at a time: 16 fully used 32-byte sectors per load, and its
-// shared-memory stores fill two 128-byte K chunks without bank conflicts.
+// A operand (r, k) = X[row0 + r][k] rounded to BF16, rows at or past `rows` zero, by the
+// producer warps (pw = 0..7).  A warp moves 8 rows x 16 floats at a time: 16 fully used
+// 32-byte sectors per load; each half-warp stores one 128-byte run of one K chunk.
 __device__ __forceinline__ void fwd_stage_x(unsigned char *dst, const float *__restrict__ X, int64_t row0, int rows,
-                                            int warp, int lane)
+                                            int pw, int lane)
 {
     constexpr int CG = kIn / 16;                               // 16-float groups per row
-    constexpr int PER = (kFwdRows / 8) * CG / (kFwdThreads / 32);
+    constexpr int PER = (kFwdRows / 8) * CG / kFwdProdWarps;   // units per warp
     constexpr int BATCH = 12;                                  // loads in flight per thread
-    static_assert((kFwdRows / 8) * CG % (kFwdThreads / 32) == 0 && PER % BATCH == 0, "X staging split");
-    const int ri = lane >> 2, ci = lane & 3;
+    static_assert((kFwdRows / 8) * CG % kFwdProdWarps == 0 && PER % BATCH == 0, "X staging split");
+    const int half = lane >> 4, ri = (lane >> 1) & 7, lo = lane & 1;
 #pragma unroll 1
     for (int i0 = 0; i0 < PER; i0 += BATCH) {
         float4 x[BATCH];
 #pragma unroll
         for (int j = 0; j < BATCH; ++j) {
-            const int u = warp + (i0 + j) * (kFwdThreads / 32);
-            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + ci;
+            const int u = pw + (i0 + j) * kFwdProdWarps;
+            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + 2 * half + lo;
             x[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (row0 + r < rows) x[j] = __ldg(reinterpret_cast<const float4 *>(X + (row0 + r) * kIn) + c4);
         }
 #pragma unroll
         for (int j = 0; j < BATCH; ++j) {
-            const int u = warp + (i0 + j) * (kFwdThreads / 32);
-            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + ci;
-            *reinterpret_cast<uint2 *>(dst + (c4 >> 1) * kFwdChunk + r * 16 + (c4 & 1) * 8) =
+            const int u = pw + (i0 + j) * kFwdProdWarps;
+            const int r = 8 * (u / CG) + ri, c4 = 4 * (u % CG) + 2 * half + lo;
+            *reinterpret_cast<uint2 *>(dst + (c4 >> 1) * kFwdChunk + r * 16 + lo * 8) =
                 make_uint2(pack2(x[j].x, x[j].y), pack2(x[j].z, x[j].w));
         }
     }
@@ -390,22 +397,32 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
                      float *__restrict__ H1out, float *__restrict__ H2out, unsigned *status)
 {
     extern __shared__ __align__(1024) unsigned char fw_sm[];
-    unsigned char *As = fw_sm;                                  // X tile; then H1 and H2
-    unsigned char *H1s = fw_sm, *H2s = fw_sm + (kH / 8) * kFwdChunk;
+    unsigned char *Xs = fw_sm, *Hs = fw_sm + kFwdOffH;
     unsigned char *W1s = fw_sm + kFwdOffW1, *W2s = fw_sm + kFwdOffW2, *W3s = fw_sm + kFwdOffW3;
     float *bias = reinterpret_cast<float *>(fw_sm + kFwdOffBias);   // b1, b2, b3
-    uint64_t *bar = reinterpret_cast<uint64_t *>(fw_sm + kFwdOffBar), *drain = bar + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(fw_sm + kFwdOffBar);
+    const uint32_t x_full = smem_addr(bars), x_empty = smem_addr(bars + 1), acc1 = smem_addr(bars + 2),
+                   h1 = smem_addr(bars + 3), acc2 = smem_addr(bars + 4), h2 = smem_addr(bars + 5),
+                   acc3 = smem_addr(bars + 6), drain = smem_addr(bars + 7);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + kFwdBars);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + kFwdBars) + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles = (rows + kFwdRows - 1) / kFwdRows;
 
-    if (warp == 0) {
+    if (warp == kFwdMmaWarp) {
         tmem_alloc(smem_addr(tmem_slot), kFwdTmemCols);
         tc_fence_before();
     }
-    if (tid == 32) {
-        mbar_init(smem_addr(bar), 1);
-        mbar_init(smem_addr(drain), 1);
+    if (tid == 0) {
+        mbar_init(x_full, kFwdProdThreads);
+        mbar_init(x_empty, 1);
+        mbar_init(acc1, 1);
+        mbar_init(h1, kFwdEpiThreads);
+        mbar_init(acc2, 1);
+        mbar_init(h2, kFwdEpiThreads);
+        mbar_init(acc3, 1);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
     }
     fwd_stage_weight(W1s, W1, kIn, kH, tid);
     fwd_stage_weight(W2s, W2, kH, kH, tid);
@@ -419,92 +436,106 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = 32 * quarter + lane;                          // row of the tile = TMEM lane
-    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
-    const uint32_t sA = smem_addr(As), sH1 = smem_addr(H1s), sH2 = smem_addr(H2s);
-    const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s), sW3 = smem_addr(W3s);
-    constexpr uint32_t idH = umma_idesc_bf16(kFwdRows, kH), idO = umma_idesc_bf16(kFwdRows, kOut);
-    uint32_t phase = 0;
-    // every thread waits for the committed MMAs; a wait that expires is recorded and
-    // the tile loop is left by all threads at the next barrier (__syncthreads_or).  The
-    // result is made warp-uniform, since the TMEM loads that follow are warp-collective.
-    auto wait_mma = [&]() -> bool {
-        const bool ok = mbar_wait(smem_addr(bar), phase, kMbarWaitLimit);
-        phase ^= 1u;
-        if (!ok && status) atomicOr(status, kStatusTimeout);
-        tc_fence_after();
-        return __all_sync(0xFFFFFFFFu, ok);
+    // a wait that expires stops every role (the others then time out or see the flag)
+    auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (mbar_wait(bar, parity, kMbarWaitLimit)) return true;
+        *abort_flag = 1;
+        if (status) atomicOr(status, kStatusTimeout);
+        return false;
     };
 
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t row0 = (int64_t)t * kFwdRows;
-        fwd_stage_x(As, X, row0, rows, warp, lane);
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll 1
-            for (int s = 0; s < kIn / 16; ++s)
-                umma_bf16(tmem, umma_desc(sA + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
-                          umma_desc(sW1 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
-            umma_commit(smem_addr(bar));
+    if (warp >= kFwdEpiWarps && warp < kFwdMmaWarp) {
+        // ------------------------------------------------------------ producers
+        const int pw = warp - kFwdEpiWarps;
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            if (*abort_flag) break;
+            if (j > 0 && !wait(x_empty, (uint32_t)((j - 1) & 1))) break;
+            fwd_stage_x(Xs, X, (int64_t)t * kFwdRows, rows, pw, lane);
+            fence_async_smem();
+            mbar_arrive(x_full);
         }
-        bool fail = !wait_mma();
-        const bool keep = row0 + r < rows;
-        if (!fail) fwd_epi_hidden(tl, 64 * half, bias, H1s, r, H1out && keep ? H1out + (row0 + r) * kH : nullptr);
-        fence_async_smem();
-        tc_fence_before();
-        if (__syncthreads_or(fail)) break;
-        if (tid == 0) {
-            tc_fence_after();
+    } else if (warp == kFwdMmaWarp) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t sX = smem_addr(Xs), sH = smem_addr(Hs);
+            const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s), sW3 = smem_addr(W3s);
+            constexpr uint32_t idH = umma_idesc_bf16(kFwdRows, kH), idO = umma_idesc_bf16(kFwdRows, kOut);
+            int j = 0;
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+                const uint32_t par = (uint32_t)(j & 1);
+                if (*abort_flag || !wait(x_full, par)) break;
+                tc_fence_after();
 #pragma unroll 1
-            for (int s = 0; s < kH / 16; ++s)
-                umma_bf16(tmem + kH, umma_desc(sH1 + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
-                          umma_desc(sW2 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
-            umma_commit(smem_addr(bar));
-        }
-        fail = !wait_mma();
-        if (!fail)
-            fwd_epi_hidden(tl + kH, 64 * half, bias + kH, H2s, r, H2out && keep ? H2out + (row0 + r) * kH : nullptr);
-        fence_async_smem();
-        tc_fence_before();
-        if (__syncthreads_or(fail)) break;
-        if (tid == 0) {
-            tc_fence_after();
+                for (int s = 0; s < kIn / 16; ++s)
+                    umma_bf16(tmem, umma_desc(sX + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                              umma_desc(sW1 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
+                umma_commit(x_empty);
+                umma_commit(acc1);
+                if (!wait(h1, par)) break;
+                tc_fence_after();
 #pragma unroll 1
-            for (int s = 0; s < kH / 16; ++s)
-                umma_bf16(tmem, umma_desc(sH2 + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
-                          umma_desc(sW3 + (uint32_t)(s * 2 * kOut * 16), kOut * 16, 128), idO, s > 0 ? 1u : 0u);
-            umma_commit(smem_addr(bar));
-        }
-        fail = !wait_mma();
-        if (!fail && half == 0) {
-            float v[16];
-            tmem_ld16(tl, v);
-            tmem_ld_wait();
-            if (row0 + r < rows) {
-                float4 *y = reinterpret_cast<float4 *>(Y + (row0 + r) * kOut);
-                const float *bo = bias + 2 * kH;
-#pragma unroll
-                for (int j = 0; j < kOut / 4; ++j)
-                    y[j] = make_float4(v[4 * j] + bo[4 * j], v[4 * j + 1] + bo[4 * j + 1], v[4 * j + 2] + bo[4 * j + 2],
-                                       v[4 * j + 3] + bo[4 * j + 3]);
+                for (int s = 0; s < kH / 16; ++s)
+                    umma_bf16(tmem + kH, umma_desc(sH + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                              umma_desc(sW2 + (uint32_t)(s * 2 * kH * 16), kH * 16, 128), idH, s > 0 ? 1u : 0u);
+                umma_commit(acc2);
+                if (!wait(h2, par)) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int s = 0; s < kH / 16; ++s)
+                    umma_bf16(tmem + 2 * kH, umma_desc(sH + (uint32_t)(s * 2 * kFwdChunk), kFwdChunk, 128),
+                              umma_desc(sW3 + (uint32_t)(s * 2 * kOut * 16), kOut * 16, 128), idO, s > 0 ? 1u : 0u);
+                umma_commit(acc3);
             }
+            // every MMA issued has completed before the tensor memory is released
+            umma_commit(drain);
+            wait(drain, 0u);
         }
-        tc_fence_before();
-        if (__syncthreads_or(fail)) break;
-    }
-    // every MMA issued has completed before the tensor memory is released
-    if (tid == 0) {
-        umma_commit(smem_addr(drain));
-        if (!mbar_wait(smem_addr(drain), 0u, kMbarWaitLimit) && status) atomicOr(status, kStatusTimeout);
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3, half = warp >> 2;
+        const int r = 32 * quarter + lane;                      // row of the tile = TMEM lane
+        const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const uint32_t par = (uint32_t)(j & 1);
+            const int64_t row = (int64_t)t * kFwdRows + r;
+            const bool keep = row < rows;
+            // warp-uniform decisions: the TMEM loads below are warp-collective
+            if (!__all_sync(0xFFFFFFFFu, !*abort_flag && wait(acc1, par))) break;
+            tc_fence_after();
+            fwd_epi_hidden(tl, 64 * half, bias, Hs, r, H1out && keep ? H1out + row * kH : nullptr);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(h1);
+            if (!__all_sync(0xFFFFFFFFu, wait(acc2, par))) break;
+            tc_fence_after();
+            fwd_epi_hidden(tl + kH, 64 * half, bias + kH, Hs, r, H2out && keep ? H2out + row * kH : nullptr);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(h2);
+            if (!__all_sync(0xFFFFFFFFu, wait(acc3, par))) break;
+            tc_fence_after();
+            if (half == 0) {
+                float v[16];
+                tmem_ld16(tl + 2 * kH, v);
+                tmem_ld_wait();
+                if (keep) {
+                    float4 *y = reinterpret_cast<float4 *>(Y + row * kOut);
+                    const float *bo = bias + 2 * kH;
+#pragma unroll
+                    for (int q = 0; q < kOut / 4; ++q)
+                        y[q] = make_float4(v[4 * q] + bo[4 * q], v[4 * q + 1] + bo[4 * q + 1],
+                                           v[4 * q + 2] + bo[4 * q + 2], v[4 * q + 3] + bo[4 * q + 3]);
+                }
+            }
+            tc_fence_before();
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, kFwdTmemCols);
+    if (warp == kFwdMmaWarp) tmem_dealloc(tmem, kFwdTmemCols);
 }
 
 // ---------------------------------------------------------------------------

@@ -75,6 +75,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(mbar) : "memory");
+}
+
 // Wait for the phase with the given parity to complete; gives up after `limit`
 // polls and returns false (the caller records a timeout instead of hanging).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit)

@@ -185,11 +185,6 @@ constexpr int kT6ERing = 8;
 constexpr int kT6BarBytes = 8 * (2 * kT6Stages + 2 + 2 + kT6ERing + 1);
 constexpr int kT6SmemBytes = kT5BBytes + kT6Stages * kT5ABytes + kT6BarBytes + 4 * (kT6ERing + 2 * kT6MaxProdWarps + 4);
 
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(mbar) : "memory");
-}
-
 // barrier 1 among the NPROD producer threads with an OR of a predicate over them
 template <int NPROD>
 __device__ __forceinline__ bool producers_sync_or(bool p)
