@@ -209,3 +209,20 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             hl.load(str(tmp_path / "libhl.so"))
     finally:
         hl._lib = saved
+
+
+def test_header_compiles_and_links_as_c99(lib, tmp_path):
+    """A plain C99 program (tests/c_abi_check.c) includes include/hl.h with -pedantic -Werror,
+    links against libhl.so and checks the argument validation of several entry points."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(B.LIB)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L" + libdir, "-lhl",
+                    "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
