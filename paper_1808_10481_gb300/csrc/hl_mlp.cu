@@ -946,9 +946,13 @@ extern "C" int hl_mlp_forward(hl_mlp *h, const float *X_dev, int rows, float *Y_
     if (rc) return rc;
     if (rows < 0 || (!X_dev && rows) || (!Y_dev && rows)) return mlp_err(h, HL_EINVAL, "bad forward arguments");
     if (rows == 0) return HL_OK;
+    // the tensor-core kernel needs no workspace; the GEMM path keeps H1 and H2 in it
+    bool fused = false;
+    MLP_CK(h, forward_fused(h->w, X_dev, rows, Y_dev, nullptr, nullptr, h->status, h->stream, &fused));
+    if (fused) return HL_OK;
     rc = ensure_rows(h, rows);
     if (rc) return rc;
-    MLP_CK(h, forward_any(h, X_dev, rows, Y_dev, h->status, h->stream));
+    MLP_CK(h, forward_into(h, X_dev, rows, work_ptrs(h, rows), Y_dev, h->stream));
     return HL_OK;
 }
 
