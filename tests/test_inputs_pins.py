@@ -123,3 +123,41 @@ def test_a_planted_generator_error_fails_the_pin(monkeypatch):
     monkeypatch.setattr(I, "_fact", lambda a: 1.0 if a == 2 else good(a))
     with pytest.raises(AssertionError):
         test_gaussian_pulse_slots_are_the_scaled_derivatives()
+
+
+def test_modified_scheme_standing_mode_on_both_grids():
+    """Both fields on both grids (the modified scheme's state): p = sin(2 pi w x) cos(2 pi w t),
+    u = -cos(2 pi w x) sin(2 pi w t), primal at t0 and dual at t0 + dt/2."""
+    m, n, dt, w, t0 = 3, 12, 0.04, 2, 0.3
+    pp, up, pd, ud = I.standing_mode_1d_both_grids(m, n, dt, w, t0=t0)
+    kap = 2 * sp.pi * w
+    p = sp.sin(kap * X[0]) * sp.cos(kap * T)
+    u = -sp.cos(kap * X[0]) * sp.sin(kap * T)
+    assert sp.simplify(sp.diff(p, T) + sp.diff(u, X[0])) == 0
+    assert sp.simplify(sp.diff(u, T) + sp.diff(p, X[0])) == 0
+    for arr, expr, dual, t in ((pp, p, False, t0), (up, u, False, t0), (pd, p, True, t0 + 0.5 * dt),
+                               (ud, u, True, t0 + 0.5 * dt)):
+        _check(arr, expr, 1, m, [n], [0, 5, n - 1], dual, t)
+
+
+def test_variable_speed_inputs():
+    """The variable-speed workload: the Taylor table of c^2 = 1 + sin(2 pi x)/2 (degree 2m+1),
+    the initial data of p = u = sin(2 pi (x - t)), and the scaled Taylor coefficients of the
+    time derivatives of the forcing z = pi sin(2 pi x) cos(2 pi (x - t)), which makes that pair
+    an exact solution of p_t + c^2 u_x = z, u_t + p_x = 0."""
+    m, n, dt, t = 2, 10, 0.03, 0.17
+    x = X[0]
+    c2 = 1 + sp.sin(2 * sp.pi * x) / 2
+    sol = sp.sin(2 * sp.pi * (x - T))
+    z = sp.pi * sp.sin(2 * sp.pi * x) * sp.cos(2 * sp.pi * (x - T))
+    assert sp.simplify(sp.diff(sol, T) + c2 * sp.diff(sol, x) - z) == 0
+    assert sp.simplify(sp.diff(sol, T) + sp.diff(sol, x)) == 0
+    A = 2 * m + 2
+    for dual in (False, True):
+        _check(I.c2_taylor_table(n, m, dual), c2, 1, A - 1, [n], [0, 3, n - 1], dual, 0.0)
+    p, u, fp, fd = I.variable_speed_wave(m, n, dt)
+    _check(p, sol, 1, m, [n], [0, 4, n - 1], False, 0.0)
+    _check(u, sol, 1, m, [n], [0, 4, n - 1], True, 0.5 * dt)
+    for forcing, dual in ((fp, False), (fd, True)):
+        for k in range(3):
+            _check(forcing(k, t), sp.diff(z, T, k), 1, A - 1, [n], [0, 7], dual, t)
